@@ -1,0 +1,367 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test checks the oracle against something other than itself: numerical quadrature of the
+spherical-means solution (Methods, Eq. pa_wave / the surface integral I), the initial-value
+problem the two-term pressure solves, brute force over every sample on tiny inputs, the
+adjoint identity, central finite differences, numpy's convolution, and torch's Adam and
+CosineAnnealingWarmRestarts.  A plausible slip in the oracle (a dropped term, a sign, an index,
+a transposed operand) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_03893_gb300 import synth
+
+
+# ---------------------------------------------------------------- quadrature helpers (test-only)
+
+def _frame(axis):
+    e3 = np.asarray(axis, float) / np.linalg.norm(axis)
+    tmp = np.array([1.0, 0.0, 0.0]) if abs(e3[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(e3, tmp)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(e3, e1)
+    return e1, e2, e3
+
+
+def sphere_quadrature(f, centre, radius, axis=(0, 0, 1), theta_max=math.pi, n_theta=300, n_phi=300):
+    """Integral of f over the sphere |x - centre| = radius: Gauss-Legendre in the polar angle on
+    [0, theta_max] about `axis`, trapezoid rule in the azimuth (both generic, no symmetry)."""
+    e1, e2, e3 = _frame(axis)
+    xg, wg = np.polynomial.legendre.leggauss(n_theta)
+    th = 0.5 * theta_max * (xg + 1.0)
+    wth = 0.5 * theta_max * wg
+    ph = np.arange(n_phi) * (2 * math.pi / n_phi)
+    wph = 2 * math.pi / n_phi
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dirs = (np.sin(T)[..., None] * (np.cos(P)[..., None] * e1 + np.sin(P)[..., None] * e2)
+            + np.cos(T)[..., None] * e3)
+    X = np.asarray(centre, float) + radius * dirs
+    W = (wth[:, None] * wph) * radius ** 2 * np.sin(T)
+    return float(np.sum(W * f(X)))
+
+
+def gaussian_field(centres, sigmas, amps):
+    centres = np.atleast_2d(centres)
+
+    def f(X):
+        out = np.zeros(X.shape[:-1])
+        for c, s, a in zip(centres, np.broadcast_to(sigmas, len(centres)), amps):
+            out += a * np.exp(-np.sum((X - c) ** 2, -1) / (2 * s * s))
+        return out
+    return f
+
+
+def d4(fun, t, h):
+    """Fourth-order central difference of fun at t."""
+    return (-fun(t + 2 * h) + 8 * fun(t + h) - 8 * fun(t - h) + fun(t - 2 * h)) / (12 * h)
+
+
+# ---------------------------------------------------------------- Eq. (sphere_int)
+
+@pytest.mark.parametrize("r,rp", [(1.0, 0.9), (1.0, 1.5), (1.0, 0.2), (2.0, 2.1)])
+def test_sphere_integral_matches_quadrature(r, rp):
+    A, sigma = 1.3, 0.3
+    u = np.array([0.3, -0.5, 0.81])
+    u /= np.linalg.norm(u)
+    det = np.array([0.1, 0.2, -0.3])
+    c = det + r * u
+    quad = sphere_quadrature(gaussian_field(c, sigma, [A]), det, rp, axis=(0, 0, 1),
+                             n_theta=400, n_phi=400)
+    closed = oracle.sphere_integral(A, sigma, r, rp)
+    assert abs(closed - quad) <= 1e-10 * abs(quad)
+
+
+# ---------------------------------------------------------------- two-term pressure (Methods)
+
+@pytest.mark.parametrize("vt", [0.5, 0.9, 1.0, 1.2, 1.6])
+def test_pressure_exact_matches_spherical_means(vt):
+    """p = (1/4 pi v) d/dt[(1/vt) I], with I from quadrature (not from the closed form)."""
+    A, sigma, r, v = 1.3, 0.3, 1.0, 1.5
+    det = np.zeros(3)
+    c = np.array([0.0, 0.6, 0.8]) * r
+    field = gaussian_field(c, sigma, [A])
+
+    def mean_term(t):
+        return sphere_quadrature(field, det, v * t, axis=c, n_theta=300, n_phi=64) / (v * t)
+    t = vt / v
+    p_quad = d4(mean_term, t, 1e-3) / (4 * math.pi * v)
+    p = oracle.pressure_exact(A, sigma, r, t, v)
+    assert abs(p - p_quad) <= 1e-8 * A
+
+
+def test_pressure_exact_initial_value_problem():
+    """The two-term pressure solves the 3-D wave equation with p(.,0) the Gaussian and
+    dp/dt(.,0) = 0 (the photoacoustic initial-value problem): check p(r,0), p_t(r,0) and
+    that u = r p satisfies u_tt = v^2 u_rr (radial d'Alembert form)."""
+    A, sigma, v = 0.7, 0.2, 1.5
+    for r in [0.05, 0.3, 0.8, 2.0]:
+        assert abs(oracle.pressure_exact(A, sigma, r, 0.0, v) - A * math.exp(-r * r / (2 * sigma ** 2))) < 1e-15
+        pt = d4(lambda t: oracle.pressure_exact(A, sigma, r, t, v), 0.0, 1e-3)
+        assert abs(pt) < 1e-10
+    u = lambda r, t: r * oracle.pressure_exact(A, sigma, r, t, v)
+    for r, t in [(0.5, 0.2), (1.0, 0.5), (0.7, 0.45), (1.3, 0.9)]:
+        h = 1e-3
+        utt = (-u(r, t + 2 * h) + 16 * u(r, t + h) - 30 * u(r, t) + 16 * u(r, t - h) - u(r, t - 2 * h)) / (12 * h * h)
+        urr = (-u(r + 2 * h, t) + 16 * u(r + h, t) - 30 * u(r, t) + 16 * u(r - h, t) - u(r - 2 * h, t)) / (12 * h * h)
+        assert abs(utt - v * v * urr) < 1e-6 * (abs(utt) + 1.0)
+
+
+def test_outgoing_is_exact_minus_incoming_and_dominates_far_field():
+    A, sigma, v = 1.0, 0.1e-3, 1500.0
+    r = 20e-3
+    for d in np.linspace(-0.3e-3, 0.3e-3, 7):
+        t = (r - d) / v
+        p_ex = oracle.pressure_exact(A, sigma, r, t, v)
+        p_out = oracle.pressure_outgoing(A, sigma, r, t, v)
+        assert abs(p_ex - p_out) <= 1e-300 + 1e-15 * abs(p_ex)
+    # near field: the incoming term is visible and has the sign of (r + vt) > 0
+    r, t = 0.1e-3, 0.05e-3 / v
+    assert oracle.pressure_exact(A, sigma, r, t, v) > oracle.pressure_outgoing(A, sigma, r, t, v)
+
+
+# ---------------------------------------------------------------- forward operator
+
+def _cluster():
+    g = synth.centred_grid(2, 2, 2, 0.3e-3, sigma=0.25e-3)
+    rng = np.random.default_rng(11)
+    A = rng.uniform(0.5, 1.5, g.M).astype(np.float32)
+    return g, A
+
+
+def test_forward_exact_matches_spherical_means_of_summed_field():
+    """Linearity (Methods: the detected wave is the superposition): the oracle forward in
+    exact mode equals quadrature of Eq. (pa_wave) applied to the summed initial field."""
+    g, A = _cluster()
+    G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, A)
+    sensors = np.array([[0.4e-3, -0.2e-3, -3.0e-3], [2.5e-3, 1.0e-3, 1.2e-3]], np.float32)
+    v, fs, t0, Nt = 1500.0, 40e6, 0.0, 128
+    y = oracle.forward(G, sensors, v, fs, t0, Nt, mode="exact")
+    field = gaussian_field(G.c, G.sigma, G.A)
+    worst = 0.0
+    for j, s in enumerate(sensors.astype(np.float64)):
+        axis = -s
+        for n in [60, 70, 78, 85, 95, 104]:
+            t = t0 + n / fs
+
+            def mean_term(tt):
+                return sphere_quadrature(field, s, v * tt, axis=axis, theta_max=math.pi / 2,
+                                         n_theta=240, n_phi=240) / (v * tt)
+            p = d4(mean_term, t, 2e-10) / (4 * math.pi * v)
+            worst = max(worst, abs(p - y[j, n]))
+    assert worst <= 1e-7 * np.max(np.abs(y))
+
+
+def test_forward_windowed_wide_window_equals_exact_far_field():
+    w = synth.tiny(1)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(w.M, 64, replace=False)
+    G = oracle.gaussians_from_grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.ox, w.grid.oy, w.grid.oz,
+                                   w.grid.h, w.grid.sigma, np.zeros(w.M, np.float32))
+    G = oracle.Gaussians(G.c[idx], G.sigma[idx], rng.uniform(0.2, 1.0, 64))
+    sens = w.sensors[:8]
+    y_ex = oracle.forward(G, sens, w.v, w.fs, w.t0, w.Nt, mode="exact")
+    y_w = oracle.forward(G, sens, w.v, w.fs, w.t0, w.Nt, k=40.0)
+    assert np.linalg.norm(y_w - y_ex) <= 1e-12 * np.linalg.norm(y_ex)
+    # the 3-sigma window drops only the Gaussian tails: small but non-zero change
+    y3 = oracle.forward(G, sens, w.v, w.fs, w.t0, w.Nt, k=3.0)
+    rel = np.linalg.norm(y3 - y_ex) / np.linalg.norm(y_ex)
+    assert 1e-4 < rel < 0.1
+
+
+@pytest.mark.parametrize("t0", [0.0, 0.37e-6])
+def test_forward_window_membership_brute_force(t0):
+    """Single Gaussians: the non-zero samples are exactly {n : |R - v t_n| <= k sigma},
+    checked against every sample index (brute force), including R near the array ends."""
+    v, fs, Nt, k, sigma = 1500.0, 40e6, 600, 3.0, 0.1e-3
+    rng = np.random.default_rng(3)
+    n_all = np.arange(Nt)
+    for R in list(rng.uniform(1e-3, 23e-3, 25)) + [v * (t0 + 3 / fs), v * (t0 + (Nt - 2) / fs)]:
+        G = oracle.Gaussians(np.array([[0.0, 0.0, R]]), np.array([sigma]), np.array([1.0]))
+        y = oracle.forward(G, np.zeros((1, 3), np.float32), v, fs, t0, Nt, k=k)[0]
+        d = R - v * (t0 + n_all / fs)
+        inside = np.abs(d) <= k * sigma
+        nz = (y != 0.0) | (np.abs(d) < 1e-15)   # d == 0 exactly gives a zero sample
+        assert np.array_equal(nz, inside)
+
+
+def test_forward_ambiguity_bound_flags_boundary_samples():
+    v, fs, t0, Nt, k, sigma = 1500.0, 40e6, 0.0, 800, 3.0, 0.1e-3
+    n0 = 500
+    R = v * (t0 + n0 / fs) + k * sigma           # sample n0 sits exactly on the window edge
+    G = oracle.Gaussians(np.array([[R, 0.0, 0.0]]), np.array([sigma]), np.array([2.0]))
+    y, amb = oracle.forward(G, np.zeros((1, 3), np.float32), v, fs, t0, Nt, k=k, tau=1e-9, want_amb=True)
+    assert amb[0, n0] > 0 and np.count_nonzero(amb) <= 2
+    assert amb[0, n0] == pytest.approx(abs(oracle.pressure_outgoing(2.0, sigma, R, n0 / fs, v)), rel=1e-6)
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _small_free(seed, M=96, Nd=12, Nt=1024):
+    g = synth.centred_grid(8, 4, 3, 0.15e-3)
+    cx, cy, cz, sg, A = synth.free_gaussians(g, seed, jitter=0.05e-3)
+    A = np.random.default_rng(seed).uniform(0.1, 1.0, g.M).astype(np.float32)
+    G = oracle.gaussians_from_soa(cx, cy, cz, sg, A)
+    sens = synth.cap_sensors(Nd, 20e-3, 160.0)
+    return G, sens, 1500.0, 40e6, 0.0, Nt
+
+
+@pytest.mark.parametrize("k", [3.0, 6.0])
+def test_adjoint_identity(k):
+    G, sens, v, fs, t0, Nt = _small_free(7)
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=G.M)
+    dl = rng.normal(size=(len(sens), Nt))
+    Fx = oracle.forward(G, sens, v, fs, t0, Nt, k=k, A=x)
+    FTd = oracle.adjoint(G, sens, v, fs, t0, Nt, dl, k=k)["A"]
+    lhs, rhs = float(np.sum(Fx * dl)), float(x @ FTd)
+    assert abs(lhs - rhs) <= 1e-12 * (np.linalg.norm(Fx) * np.linalg.norm(dl))
+
+
+def test_adjoint_centre_and_sigma_gradients_match_central_fd():
+    """Gradients of L = <delta, F(c, sigma) A> against central differences of the oracle
+    forward, at k = 10 where the moving window edge carries no weight."""
+    G, sens, v, fs, t0, Nt = _small_free(13, Nt=1024)
+    k = 10.0
+    rng = np.random.default_rng(17)
+    dl = rng.normal(size=(len(sens), Nt))
+    grads = oracle.adjoint(G, sens, v, fs, t0, Nt, dl, k=k, want=("A", "c", "sigma"))
+
+    def L(Gx):
+        return float(np.sum(oracle.forward(Gx, sens, v, fs, t0, Nt, k=k) * dl))
+    for i in rng.choice(G.M, 6, replace=False):
+        for ax in range(3):
+            hstep = 1e-6 * 1e-3
+            Gp = oracle.Gaussians(G.c.copy(), G.sigma.copy(), G.A.copy())
+            Gm = oracle.Gaussians(G.c.copy(), G.sigma.copy(), G.A.copy())
+            Gp.c[i, ax] += hstep
+            Gm.c[i, ax] -= hstep
+            fd = (L(Gp) - L(Gm)) / (2 * hstep)
+            assert abs(fd - grads["c"][ax, i]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grads["c"]).max())
+        hs = 1e-6 * G.sigma[i]
+        Gp = oracle.Gaussians(G.c.copy(), G.sigma.copy(), G.A.copy())
+        Gm = oracle.Gaussians(G.c.copy(), G.sigma.copy(), G.A.copy())
+        Gp.sigma[i] += hs
+        Gm.sigma[i] -= hs
+        fd = (L(Gp) - L(Gm)) / (2 * hs)
+        assert abs(fd - grads["sigma"][i]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grads["sigma"]).max())
+
+
+# ---------------------------------------------------------------- voxelize
+
+@pytest.mark.parametrize("k,ntap", [(3.0, 3), (2.5, 2)])
+def test_voxelize_grid_case_is_separable_convolution(k, ntap):
+    g = synth.centred_grid(10, 7, 6, 0.1e-3)
+    A = np.random.default_rng(2).uniform(0, 1, g.M).astype(np.float32)
+    G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, A)
+    vol = oracle.voxelize(G, k, g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h)
+    taps = np.exp(-np.arange(-ntap, ntap + 1) ** 2 / 2.0)
+    ref = A.astype(np.float64).reshape(g.nz, g.ny, g.nx)
+    for axis in range(3):
+        ref = np.apply_along_axis(lambda r: np.convolve(r, taps, mode="full")[ntap:ntap + r.size], axis, ref)
+    assert np.max(np.abs(vol - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_voxelize_free_centres_brute_force():
+    rng = np.random.default_rng(4)
+    M = 5
+    c = rng.uniform(-0.2e-3, 0.2e-3, (M, 3))
+    sg = rng.uniform(0.05e-3, 0.15e-3, M)
+    A = rng.uniform(0.5, 1.0, M)
+    G = oracle.Gaussians(c, sg, A)
+    n, h, o = 6, 0.08e-3, -0.24e-3
+    vol = oracle.voxelize(G, 3.0, n, n, n, o, o, o, h)
+    f = lambda q: float(np.float32(q))
+    ref = np.zeros((n, n, n))
+    for iz in range(n):
+        for iy in range(n):
+            for ix in range(n):
+                p = np.array([f(o) + (ix + 0.5) * f(h), f(o) + (iy + 0.5) * f(h), f(o) + (iz + 0.5) * f(h)])
+                for i in range(M):
+                    dd = p - c[i]
+                    if np.all(np.abs(dd) <= 3.0 * sg[i]):
+                        ref[iz, iy, ix] += A[i] * math.exp(-float(dd @ dd) / (2 * sg[i] ** 2))
+    assert np.max(np.abs(vol - ref)) <= 1e-13
+
+
+# ---------------------------------------------------------------- Adam, CAWR, Algorithm 2
+
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    z = rng.normal(size=50)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    zt = torch.tensor(z.copy(), requires_grad=True)
+    opt = torch.optim.Adam([zt], lr=0.03, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(1, 12):
+        g = rng.normal(size=50)
+        oracle.adam(z, m, v, g, t, 0.03)
+        zt.grad = torch.tensor(g)
+        opt.step()
+    assert np.max(np.abs(z - zt.detach().numpy())) <= 1e-12
+
+
+@pytest.mark.parametrize("T0,Tmult", [(10, 1.0), (4, 2.0), (3, 3.0)])
+def test_cawr_matches_torch(T0, Tmult):
+    torch = pytest.importorskip("torch")
+    p = torch.zeros(1, requires_grad=True)
+    opt = torch.optim.SGD([p], lr=0.5)
+    sch = torch.optim.lr_scheduler.CosineAnnealingWarmRestarts(opt, T_0=T0, T_mult=int(Tmult), eta_min=0.01)
+    for t in range(40):
+        assert oracle.cawr(t, 0.5, 0.01, T0, Tmult) == pytest.approx(opt.param_groups[0]["lr"], abs=1e-12)
+        opt.step()
+        sch.step()
+
+
+def _dense_problem():
+    g = synth.centred_grid(4, 4, 4, 0.2e-3)
+    G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, np.zeros(g.M, np.float32))
+    sens = synth.cap_sensors(6, 5e-3, 180.0)
+    v, fs, t0, Nt = 1500.0, 40e6, 0.0, 256
+    F = np.stack([oracle.forward(G, sens, v, fs, t0, Nt, A=np.eye(g.M)[i]).ravel() for i in range(g.M)], 1)
+    x_true = np.random.default_rng(21).uniform(0, 1, g.M)
+    b = F @ x_true
+    return G, sens, v, fs, t0, Nt, F, b
+
+
+def test_ir_adam_npc_cawr_matches_torch_autograd():
+    """Algorithm 2 (NPC, data loss |F x - b|^2 / N, Adam, CAWR) against torch autograd +
+    torch.optim on the dense matrix of the same operator."""
+    torch = pytest.importorskip("torch")
+    G, sens, v, fs, t0, Nt, F, b = _dense_problem()
+    iters, eta, T0 = 15, 0.05, 6
+    x, loss, resid = oracle.ir(G, sens, v, fs, t0, Nt, b, iters, rule="adam", npc=True,
+                               eta_max=eta, eta_min=0.001, T0=T0, Tmult=1.0)
+    Ft = torch.tensor(F)
+    bt = torch.tensor(b)
+    z = torch.zeros(G.M, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([z], lr=eta, betas=(0.9, 0.999), eps=1e-8)
+    sch = torch.optim.lr_scheduler.CosineAnnealingWarmRestarts(opt, T_0=T0, T_mult=1, eta_min=0.001)
+    tl = []
+    for t in range(iters):
+        opt.zero_grad()
+        L = torch.mean((Ft @ (z + 1e-8) ** 2 - bt) ** 2)
+        tl.append(float(L))
+        L.backward()
+        opt.step()
+        sch.step()
+    xt = ((z + 1e-8) ** 2).detach().numpy()
+    assert np.allclose(loss, tl, rtol=1e-9, atol=0)
+    assert np.max(np.abs(x - xt)) <= 1e-9 * np.max(np.abs(xt))
+    assert resid[0] == pytest.approx(np.linalg.norm(b), rel=1e-12)
+
+
+def test_ir_line_search_is_exact_minimiser():
+    G, sens, v, fs, t0, Nt, F, b = _dense_problem()
+    x, loss, resid = oracle.ir(G, sens, v, fs, t0, Nt, b, 4, rule="linesearch", npc=False)
+    assert np.all(np.diff(loss) < 0)
+    x1, _, _ = oracle.ir(G, sens, v, fs, t0, Nt, b, 1, rule="linesearch", npc=False)
+    g = F.T @ (F @ np.zeros(G.M) - b)
+    f = lambda a: float(np.sum((F @ (-a * g) - b) ** 2))
+    alpha = -x1[0] / g[0] if g[0] != 0 else -x1[1] / g[1]
+    assert np.allclose(x1, -alpha * g, rtol=1e-10)
+    assert f(alpha) <= f(alpha * 1.01) and f(alpha) <= f(alpha * 0.99)
