@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: seconds per reconstruction iteration (Algorithm 2 step: NPC, forward, FP64 loss,
+adjoint, Adam) on the paper's in-vivo scale -- 256 x 256 x 128 = 8.4 M Gaussians on a 0.1 mm
+grid, 1024 sensors, 4096 samples at 40 MHz -- with seeded synthetic data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  `value` is device time per iteration with inputs resident in
+HBM; `e2e` repeats the measurement through the public API with the measured signal copied from
+pinned host memory each step and the loss read back.  `roofline` uses the dominant kernel's own
+launch times (CUDA events on its stream, inside the timed region) against the FP32 issue rate.
+`cpu_baseline` times the FP64 oracle on a bounded sensor sample (rank 0, N = 1 only).
+With N > 1 (torchrun) every rank runs an independent replica (the path is replicated, not
+sharded, on one-GPU machines): value = max-over-ranks time / (K * N).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s per IR iteration (fwd+adjoint) at 8.4M Gaussians; pair-evals/s vs FP32 peak"
+UNIT = "s/iter"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+MUFU_LANES_PER_SM = 32          # ex2 throughput measured on this machine (lane-ops / clk / SM)
+LAUNCHES_PER_STEP = 9           # npc, slab info, forward slab, slab reduce, resid, finish, tile info, adjoint, adam
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="paper", choices=["paper", "mid", "tiny"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sensors", type=int, default=32)
+    return p.parse_args()
+
+
+def workload(name):
+    from paper_2602_03893_gb300 import synth
+    return {"paper": synth.paper_scale, "mid": synth.mid, "tiny": synth.tiny}[name]()
+
+
+def work_units(w):
+    """pair-evals and sample-evals per operator application.  Every pair's window lies inside
+    the record for these workloads; the expected number of samples in |d| <= k sigma is
+    2 k sigma / (v / fs) (an interval of that length in sample units)."""
+    pairs = float(w.M) * w.Nd
+    samples = pairs * 2.0 * w.k * w.grid.sigma * w.fs / w.v
+    return pairs, samples
+
+
+# Algorithmic FP32 work: per sample-eval 3 lane-ops (power/recurrence step of the Gaussian,
+# the kernel value d*e, the accumulation), per pair 15 lane-ops (offset distance, phase,
+# window bounds, initial exponentials' arguments, weight A / 2R); 4 MUFU ops per pair.
+ALG_OPS_PER_SAMPLE = 3.0
+ALG_OPS_PER_PAIR = 15.0
+ALG_MUFU_PER_PAIR = 4.0
+
+
+def alg_ops(w):
+    pairs, samples = work_units(w)
+    return ALG_OPS_PER_SAMPLE * samples + ALG_OPS_PER_PAIR * pairs
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2602_03893_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, src):
+    """dram bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("src_hash") == src:
+            return e.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of the device's SM clock and throttle reasons every 200 ms."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def _mine(self):
+        mine = [r for r in self.rows if self.uuid and self.uuid.lower() in r[0].lower()]
+        return mine or self.rows
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=5)
+
+    def summary(self):
+        self.rows = self._mine()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1])]
+        mx = [num(r[2]) for r in self.rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in self.rows)}
+
+
+def cpu_baseline(w, n_sensors, seed=5):
+    """The FP64 oracle (as it stands) on a bounded sample: one forward + adjoint over all
+    Gaussians and `n_sensors` sensors, extrapolated linearly to all sensors (both operators are
+    sums of independent per-sensor terms)."""
+    import oracle
+    oracle.build()
+    threads = len(os.sched_getaffinity(0))
+    oracle.set_threads(threads)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.Nd, n_sensors, replace=False))
+    sens = np.ascontiguousarray(w.sensors[idx])
+    x = (rng.uniform(0.0, 1.0, w.M) ** 2).astype(np.float32)
+    G = oracle.gaussians_from_grid(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.ox, w.grid.oy, w.grid.oz, w.grid.h,
+                                   w.grid.sigma, x)
+    delta = rng.normal(size=(n_sensors, w.Nt))
+    t0 = time.perf_counter()
+    oracle.forward(G, sens, w.v, w.fs, w.t0, w.Nt, k=w.k)
+    t1 = time.perf_counter()
+    oracle.adjoint(G, sens, w.v, w.fs, w.t0, w.Nt, delta, k=w.k)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t0) * (w.Nd / n_sensors)
+    return {"value": per_iter, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one forward + adjoint of all {w.M} Gaussians x {n_sensors} of {w.Nd} sensors "
+                      f"({t1 - t0:.1f} s + {t2 - t1:.1f} s), scaled by {w.Nd}/{n_sensors}"}
+
+
+def dist_setup(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle (CPU, FP64) timed on this machine's host cores for the same
+    metric, each step a bounded sample (a sensor subset) of the workload, scaled to all sensors."""
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    ns = max(1, min(w.Nd, args.cpu_sensors // 2))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(w, ns, seed=100 + s)
+        if s >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": w.M, "sensors": w.Nd, "samples": w.Nt,
+                       "parallelism": f"replicas{world}"},
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "value": v, "unit": UNIT,
+                             "sample": f"per step: forward + adjoint over all Gaussians x {ns} sensors, scaled by "
+                                       f"{w.Nd}/{ns}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    from paper_2602_03893_gb300 import _lib, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    g = w.grid
+    grid = _lib.Grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma)
+    A_true = torch.as_tensor(w.A, device=dev)
+    arr = _lib.SensorArray(xyz=torch.as_tensor(w.sensors, device=dev), sound_speed=w.v, fs=w.fs, n_samples=w.Nt,
+                           t0=w.t0, window_k=w.k)
+    # measured data: forward of the phantom + 30 dB noise, scaled to max |b| = 1
+    y = torch.empty((w.Nd, w.Nt), device=dev)
+    _lib.gpair_forward(_lib.Gaussians(A=A_true, grid=grid), arr, y)
+    b_np = synth.add_noise(y.cpu().numpy(), 30.0, seed=7)
+    b_np /= np.abs(b_np).max()
+    b = torch.as_tensor(b_np, device=dev)
+    b_host = torch.as_tensor(b_np).pin_memory()
+    b_dev2 = torch.empty_like(b)
+
+    iters_total = args.warmup + args.steps
+    params = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, npc_eps=1e-8, eta_max=0.02, eta_min=0.0,
+                             T0=max(1, 2 * iters_total), adam_eps=1e-20)
+    gs = _lib.Gaussians(A=A_true, grid=grid)     # the solver's amplitudes are its own iterate
+    solver = _lib.Solver(gs, arr, params)
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        solver.gpair_step(b, want_loss=False)
+    torch.cuda.synchronize()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(str(uuid) if uuid is not None else None)
+    sampler.start()
+    time.sleep(0.3)
+    solver.gpair_solver_profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.gpair_step(b, want_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.stop()
+    t_ms = e0.elapsed_time(e1)
+    (fwd_ms, adj_ms, step_ms), nrec = solver.gpair_solver_timings()
+    solver.gpair_solver_profile(False)
+    assert _lib.gpair_last_device_status() == 0, "device status word set during the timed region"
+    t_max = max_over_ranks(t_ms, world)
+    per_iter = t_max / 1e3 / (args.steps * world)
+
+    # ---- end to end through the public API with host buffers
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        b_dev2.copy_(b_host, non_blocking=True)
+        solver.gpair_step(b_dev2, want_loss=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    tw0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        b_dev2.copy_(b_host, non_blocking=True)          # H2D of the step's input (pinned)
+        loss, resid = solver.gpair_step(b_dev2, want_loss=True)   # D2H of the FP64 loss (syncs)
+    torch.cuda.synchronize()
+    tw = time.perf_counter() - tw0
+    tw = max_over_ranks(tw, world)
+    e2e = {"value": tw / (e2e_steps * world), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 4),
+           "d2h_bytes_per_step": 8, "loss_last": loss}
+
+    clocks = sampler.summary()
+    pairs, samples = work_units(w)
+    ops = alg_ops(w)
+    fwd_avg = fwd_ms / max(nrec, 1) / 1e3
+    adj_avg = adj_ms / max(nrec, 1) / 1e3
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    kern = {"forward": {"kernel": "fwd_slab_kernel", "s_per_launch": fwd_avg, "achieved_Tops": ops / fwd_avg / 1e12,
+                        "frac": ops / fwd_avg / peak},
+            "adjoint": {"kernel": "adj_kernel", "s_per_launch": adj_avg, "achieved_Tops": ops / adj_avg / 1e12,
+                        "frac": ops / adj_avg / peak}}
+    dom = "forward" if fwd_avg >= adj_avg else "adjoint"
+    src = src_hash("forward.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
+    tr = profiled_traffic(kern[dom]["kernel"], src)
+    mufu_bound = ALG_MUFU_PER_PAIR * pairs / (SM_COUNT * MUFU_LANES_PER_SM * SM_MAX_MHZ * 1e6)
+    roofline = {"bound": "alu", "achieved": ops / (fwd_avg if dom == "forward" else adj_avg) / 1e12,
+                "peak": peak / 1e12, "unit": "T FP32 lane-ops/s", "frac": kern[dom]["frac"],
+                "traffic": tr, "kernel": kern[dom]["kernel"],
+                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
+                "alg_ops_per_launch": ops, "mufu_bound_s": mufu_bound, "kernels": kern}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = kern[dom]["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, min(args.cpu_sensors, w.Nd))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": per_iter, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "gaussians": w.M, "sensors": w.Nd, "samples": w.Nt,
+                           "grid": [g.nx, g.ny, g.nz], "spacing_m": g.h, "sigma_m": g.sigma, "window_k": w.k,
+                           "fs_hz": w.fs, "sound_speed": w.v, "step": "Adam + NPC + CAWR, FP64 loss",
+                           "l2": "inputs larger than L2: A, z, m, v 33.5 MB each, y and b 16.8 MB each, "
+                                 "slab partials 75 MB",
+                           "parallelism": f"replicas{world}"},
+                "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
+                "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
+                              "step_device": step_ms / max(nrec, 1)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

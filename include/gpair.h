@@ -1,0 +1,190 @@
+/*
+ * gpair.h -- C ABI of the GB300 GPAIR forward/adjoint library (libgpair.so).
+ *
+ * GPAIR (arXiv 2602.03893) models the photoacoustic initial pressure as a sum of isotropic
+ * 3-D Gaussians (Methods, Eqs. 1-2) and derives the pressure one Gaussian produces at a point
+ * detector in closed form (Eq. single_forward):
+ *
+ *     p(R, t) = A / (2R) * d * exp(-d^2 / (2 sigma^2)),   d = R - v t,
+ *
+ * kept where |d| <= k sigma (the paper's 3-sigma principle; k = window_k, inclusive).  This
+ * library evaluates that window directly for every (Gaussian, sensor) pair -- the exact pair
+ * enumeration the Methods section describes before introducing its approximate upsampled
+ * alignment -- and its exact transpose.
+ *
+ * Units are SI throughout (metres, seconds, m/s, Hz).  Sample n of every sensor is taken at
+ * t_n = t0 + n / fs.  Signals are float32, sensor-major: y[j * n_samples + n].
+ *
+ * Memory: every data pointer is caller-owned DEVICE memory on the current CUDA device unless a
+ * field says otherwise; struct arguments themselves are host memory, read during the call
+ * only.  The library owns a per-(device, stream) scratch pool (grown on demand with
+ * cudaMalloc, released by gpair_release_scratch) and the workspace inside a gpair_solver.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ * are asynchronous on that stream; a call that returns a host scalar (gpair_step) synchronises
+ * that stream only.
+ *
+ * Errors: every entry point returns a gpair_status and never aborts or prints.  Arguments are
+ * validated before any launch (INVALID_ARG).  Device-side failures (a bounded wait that ran
+ * out, an internal capacity exceeded) set a per-stream status word that
+ * gpair_last_device_status() reads and clears.
+ *
+ * Thread safety: calls on distinct streams (or distinct solvers) may run concurrently from
+ * different host threads.
+ */
+#ifndef GPAIR_H
+#define GPAIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPAIR_OK = 0,
+    GPAIR_ERR_INVALID_ARG = 1,   /* a NULL pointer, a non-positive size, fs <= 0, k <= 0, ... */
+    GPAIR_ERR_CUDA = 2,          /* a CUDA runtime call failed (launch, copy, ...) */
+    GPAIR_ERR_NOMEM = 3,         /* scratch/workspace allocation failed */
+    GPAIR_ERR_TIMEOUT = 4,       /* a device-side bounded wait ran out (reported on the stream) */
+    GPAIR_ERR_UNSUPPORTED = 5,   /* shape outside the supported envelope (e.g. window too long) */
+    GPAIR_ERR_NONFINITE = 6      /* non-finite input detected (validation builds) */
+} gpair_status;
+
+/* Regular grid of Gaussian centres (Methods, GKD: one Gaussian per voxel centre).
+ * Centre of node (ix, iy, iz) is (ox, oy, oz) + ((ix, iy, iz) + 1/2) * dx, x fastest; index
+ * i = (iz * ny + iy) * nx + ix.  sigma is shared by all Gaussians (the paper uses sigma = dx). */
+typedef struct {
+    int nx, ny, nz;
+    float ox, oy, oz, dx;
+    float sigma;
+} gpair_grid;
+
+/* A Gaussian set.  Two layouts:
+ *  - grid-implicit: cx == NULL; `grid` (host pointer) gives centres and the shared sigma;
+ *    M must equal nx*ny*nz; only A is read (device, [M]).
+ *  - structure of arrays: cx, cy, cz, sigma, A are device float arrays of length M
+ *    (free centres and per-Gaussian widths); `grid` is ignored. */
+typedef struct {
+    int64_t M;
+    const float *cx, *cy, *cz, *sigma, *A;
+    const gpair_grid* grid;
+} gpair_gaussians;
+
+/* Sensor array and acquisition (Methods: detector positions s_j, speed of sound v, sampling
+ * rate f_s, N_t samples).  xyz is device memory [n_sensors][3]. */
+typedef struct {
+    int n_sensors;
+    const float* xyz;
+    float sound_speed;   /* v, m/s, > 0 */
+    float fs;            /* Hz, > 0 */
+    float t0;            /* time of sample 0, s (default 0) */
+    int n_samples;       /* N_t >= 1 */
+    float window_k;      /* k of the |d| <= k sigma window, > 0 (paper: 3) */
+} gpair_array;
+
+/* ----------------------------------------------------------------------------------------
+ * gpair_forward -- the forward operator y = A(x) (Eq. single_forward summed over all
+ * Gaussians; Methods, the direct pair enumeration):
+ *     y[j][n] = sum_i A_i / (2 R_ij) * d * exp(-d^2 / 2 sigma_i^2),  d = R_ij - v t_n,
+ * over |d| <= k sigma_i, R_ij = |c_i - s_j|, 0 <= n < N_t.
+ * y: device [n_sensors][n_samples] float32, fully overwritten.
+ * Returns INVALID_ARG for NULL/empty/inconsistent inputs; the call is asynchronous.
+ * Accuracy: FP32 arithmetic with the phase R - v t_n referenced to an FP64 per-(tile, sensor)
+ * origin; relative L2 error against the FP64 definition ~1e-6 (tested to 1e-5). */
+gpair_status gpair_forward(const gpair_gaussians* g, const gpair_array* arr, float* y, void* stream);
+
+/* ----------------------------------------------------------------------------------------
+ * gpair_adjoint -- the exact transpose of gpair_forward (Methods, adjoint operator: the
+ * back-projection of a detector residual delta), plus the closed-form parameter gradients of
+ * L = sum_{j,n} delta[j][n] y[j][n]:
+ *     gA[i]     = sum_{j,n} delta_j[n] * d e / (2R)
+ *     gc[a][i]  = sum_{j,n} delta_j[n] * dp/dR * (c_i,a - s_j,a) / R,
+ *                 dp/dR = -p/R + A/(2R) (1 - d^2/sigma^2) e
+ *     gsigma[i] = sum_{j,n} delta_j[n] * A/(2R) * d^3/sigma^3 * e
+ * with e = exp(-d^2/2sigma^2) and the window held fixed.  delta: device [n_sensors][n_samples].
+ * gA: device [M] (required); gc: device [3][M] planar (x, y, z rows) or NULL; gsigma: device
+ * [M] or NULL.  Outputs are overwritten.  Per-Gaussian sums over sensors use Kahan
+ * compensation; no global atomics. */
+gpair_status gpair_adjoint(const gpair_gaussians* g, const gpair_array* arr, const float* delta,
+                           float* gA, float* gc, float* gsigma, void* stream);
+
+/* ----------------------------------------------------------------------------------------
+ * gpair_voxelize -- Eq. (2) sampled on a voxel grid (Methods, the continuous source field):
+ *     V[v] = sum_i A_i prod_a [|r_a - c_a| <= k sigma_i] exp(-(r_a - c_a)^2 / 2 sigma_i^2)
+ * at voxel centres of out_grid (host pointer; its sigma field is ignored), box-truncated at
+ * k sigma_i per axis with k = window_k.  vol: device [nz][ny][nx] float32, overwritten.
+ * Grid-implicit Gaussians on the same lattice use three separable 1-D passes; any other set
+ * uses a cell-binned gather. */
+gpair_status gpair_voxelize(const gpair_gaussians* g, const gpair_grid* out_grid, float window_k,
+                            float* vol, void* stream);
+
+/* ----------------------------------------------------------------------------------------
+ * Reconstruction step (Algorithm 2: NPC, forward, loss, adjoint, chain rule, CAWR, Adam). */
+typedef enum { GPAIR_RULE_ADAM = 0, GPAIR_RULE_GD_LINESEARCH = 1 } gpair_rule;
+
+typedef struct {
+    int rule;            /* gpair_rule */
+    int npc;             /* 1: x = (z + npc_eps)^2 (Methods, nonnegative parameterisation) */
+    float npc_eps;       /* paper: 1e-8 */
+    float eta_max, eta_min;  /* CAWR learning-rate range */
+    int T0;              /* first restart period (iterations) */
+    float T_mult;        /* period multiplier (>= 1) */
+    float beta1, beta2, adam_eps;
+} gpair_step_params;
+
+typedef struct gpair_solver gpair_solver;
+
+/* Create a solver for amplitudes only: centres/widths come from g (grid or SoA; the SoA arrays
+ * must stay valid while the solver lives); g->A is ignored.  The solver owns z, Adam m and v
+ * (zero-initialised, Algorithm 2 step 1), the iteration counter and workspace (y, residual,
+ * gradient, FP64 reduction scratch).  Allocates device memory on the current device. */
+gpair_status gpair_solver_create(const gpair_gaussians* g, const gpair_array* arr,
+                                 const gpair_step_params* params, gpair_solver** out);
+void gpair_solver_destroy(gpair_solver* s);
+
+/* One iteration of Algorithm 2 with the exact data-term gradient 2 (y - b) / N, N = Nd Nt.
+ * b: device [n_sensors][n_samples].  loss_out / resid_out (host, may be NULL) receive the FP64
+ * loss |y - b|^2 / N and |y - b| of the iterate entering the step; when either is non-NULL the
+ * call synchronises `stream`.  The reductions are done in FP64 on the GPU. */
+gpair_status gpair_step(gpair_solver* s, const float* b, double* loss_out, double* resid_out,
+                        void* stream);
+
+/* Current image x = phi(z) (device [M] float32, written asynchronously). */
+gpair_status gpair_solver_image(gpair_solver* s, float* x_out, void* stream);
+/* Latent z, Adam moments m, v (device [M] each, any may be NULL) and the iteration count:
+ * copies out (get) or in (set), for checkpoint / resume.  set with z != NULL also allows a
+ * warm start. */
+gpair_status gpair_solver_get_state(gpair_solver* s, float* z, float* m, float* v, int* t, void* stream);
+gpair_status gpair_solver_set_state(gpair_solver* s, const float* z, const float* m, const float* v,
+                                    int t, void* stream);
+
+/* Device-side timing of gpair_step (tracing).  enable != 0: every following step records CUDA
+ * events on its own stream around the forward slab kernel, the adjoint kernel and the whole
+ * step.  gpair_solver_timings synchronises on the last recorded event, writes the summed
+ * milliseconds ms[0] = forward slab kernel, ms[1] = adjoint kernel, ms[2] = whole step and the
+ * number of recorded steps (may be NULL), and clears the record. */
+gpair_status gpair_solver_profile(gpair_solver* s, int enable);
+gpair_status gpair_solver_timings(gpair_solver* s, double* ms /*[3]*/, int* nsteps);
+
+/* ----------------------------------------------------------------------------------------
+ * FP64 reductions on the device (used by the step and exported for tests):
+ * out[0] = sum (a - b)^2, out[1] = sum a*b'  where b' = c (dot with a third vector; c may be
+ * NULL then out[1] = 0).  a, b, c: device float [n]; out: device double [2]. */
+gpair_status gpair_reduce_f64(const float* a, const float* b, const float* c, int64_t n,
+                              double* out, void* stream);
+
+/* Misc. */
+const char* gpair_status_string(gpair_status s);
+/* Reads and clears the device status word of `stream` (synchronises that stream). */
+gpair_status gpair_last_device_status(void* stream);
+/* Frees the scratch pool of every stream on the current device. */
+void gpair_release_scratch(void);
+/* Library version string. */
+const char* gpair_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPAIR_H */

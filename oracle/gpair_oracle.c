@@ -197,7 +197,9 @@ void ora_voxelize(int64_t M, const double* cx, const double* cy, const double* c
      * accumulation order is fixed. */
     for (int64_t i = 0; i < M; ++i) {
         if (A[i] == 0.0) continue;
-        double half = k * sg[i], s2 = 2.0 * sg[i] * sg[i];
+        /* The box edge is inclusive; a relative 1e-12 slack keeps lattice ties (|m h| == k s
+         * exactly in real arithmetic) inside despite double rounding of the centre differences. */
+        double half = k * sg[i] * (1.0 + 1e-12), s2 = 2.0 * sg[i] * sg[i];
         long xa = (long)floor((cx[i] - half - ox) / h - 0.5) - 1, xb = (long)ceil((cx[i] + half - ox) / h - 0.5) + 1;
         long ya = (long)floor((cy[i] - half - oy) / h - 0.5) - 1, yb = (long)ceil((cy[i] + half - oy) / h - 0.5) + 1;
         long za = (long)floor((cz[i] - half - oz) / h - 0.5) - 1, zb = (long)ceil((cz[i] + half - oz) / h - 0.5) + 1;

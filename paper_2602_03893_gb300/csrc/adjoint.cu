@@ -1,0 +1,177 @@
+// adjoint.cu -- exact transpose of the windowed forward operator and the closed-form
+// gradients with respect to amplitude, centre and width (Methods, adjoint operator; the
+// derivatives of Eq. single_forward).
+//
+// Work decomposition: one CTA per tile of 256 Gaussians, one thread per Gaussian.  The CTA
+// walks all sensors in chunks of 32: warp 0 forms the 32 FP64 (tile, sensor) references, the
+// CTA stages each sensor's residual band (the samples the tile can touch) in shared memory,
+// and every thread gathers its own pair windows from those bands.  Each Gaussian's sums over
+// sensors are Kahan-compensated in registers and written once: no atomics of any kind.
+#include "gpair_internal.cuh"
+
+namespace gp {
+
+constexpr int ADJ_THREADS = TILE;
+constexpr int ADJ_SC = 32;   // sensors staged per chunk
+
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+
+// Window sums of one pair: s1 = sum dl d e (amplitude gradient); with FULL also s0 = sum dl e,
+// s2 = sum dl d^2 e, s3 = sum dl d^3 e (centre and width gradients).  src[m] is the residual at
+// sample n0 + m; d = phi - m Delta is the pair's phase there.
+template <bool FULL>
+__device__ __forceinline__ void window_sums(const float* __restrict__ src, int m_lo, int m_hi, float phi,
+                                            float Delta, float c2, float& s0, float& s1, float& s2, float& s3) {
+    for (int m = m_lo; m <= m_hi; ++m) {
+        const float d = fmaf(-(float)m, Delta, phi);
+        const float e = ex2_approx(d * d * c2);
+        const float u = src[m] * e;
+        if (FULL) {
+            const float ud = u * d;
+            s0 += u;
+            s1 += ud;
+            const float udd = ud * d;
+            s2 += udd;
+            s3 = fmaf(udd, d, s3);
+        } else {
+            s1 = fmaf(u, d, s1);
+        }
+    }
+}
+
+template <bool GRID, bool FULL>
+__global__ void __launch_bounds__(ADJ_THREADS)
+adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* __restrict__ delta,
+           float* __restrict__ gA, float* __restrict__ gc, float* __restrict__ gs, int LBA) {
+    extern __shared__ __align__(16) float bands[];   // [ADJ_SC][LBA]
+    __shared__ PairRef refs[ADJ_SC];
+    __shared__ int nbs[ADJ_SC];
+
+    const int64_t t = blockIdx.x;
+    const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
+    const TileInfo rt = ti[t];
+
+    // This thread's Gaussian: index, amplitude, width and offset from the tile reference.
+    bool valid;
+    int64_t i;
+    float Ai, sig, dx, dy, dz;
+    double c0x, c0y, c0z;
+    if (GRID) {
+        const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
+        const int gx = tx * BX + (l & (BX - 1)), gy = ty * BY + ((l / BX) & (BY - 1)), gz = tz * BZ + l / (BX * BY);
+        valid = gx < g.nx && gy < g.ny && gz < g.nz;
+        i = ((int64_t)gz * g.ny + gy) * g.nx + gx;
+        Ai = valid ? g.A[i] : 0.f;
+        sig = g.sigma;
+        brick_offset(l, g.h, dx, dy, dz);
+        c0x = g.ox + (tx * BX + BX / 2) * (double)g.h;
+        c0y = g.oy + (ty * BY + BY / 2) * (double)g.h;
+        c0z = g.oz + (tz * BZ + BZ / 2) * (double)g.h;
+    } else {
+        i = t * TILE + l;
+        valid = i < g.M;
+        Ai = valid ? g.A[i] : 0.f;
+        sig = valid ? g.sg[i] : 1.f;
+        dx = valid ? g.cx[i] - rt.c0x : 0.f;
+        dy = valid ? g.cy[i] - rt.c0y : 0.f;
+        dz = valid ? g.cz[i] - rt.c0z : 0.f;
+        c0x = rt.c0x; c0y = rt.c0y; c0z = rt.c0z;
+    }
+    const float c2 = -0.72134752044448170368f / (sig * sig);   // -log2(e) / (2 sigma^2)
+    const float ks = a.k * sig;
+    const float Delta = a.Delta, invDelta = a.invDelta;
+    const float reach = rt.rad + a.k * rt.smax;                // farthest |d| offset in the tile
+
+    KahanF kA, kX, kY, kZ, kS;
+    for (int j0 = 0; j0 < a.Nd; j0 += ADJ_SC) {
+        const int nsc = min(ADJ_SC, a.Nd - j0);
+        if (warp == 0 && lane < nsc) {
+            const int j = j0 + lane;
+            const PairRef r = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+            refs[lane] = r;
+            nbs[lane] = (r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2) & ~3;
+        }
+        __syncthreads();
+        for (int idx = l; idx < nsc * LBA; idx += ADJ_THREADS) {
+            const int q = idx / LBA, n = nbs[q] + (idx - q * LBA);
+            bands[idx] = (n >= 0 && n < a.Nt) ? delta[(size_t)(j0 + q) * a.Nt + n] : 0.f;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int q = 0; q < nsc; ++q) {
+                const PairRef r = refs[q];
+                float R, phi;
+                pair_phase(r, dx, dy, dz, R, phi);
+                const int m_lo = max((int)ceilf((phi - ks) * invDelta), -r.n0);
+                const int m_hi = min((int)floorf((phi + ks) * invDelta), a.Nt - 1 - r.n0);
+                const int off = r.n0 - nbs[q];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                if ((off + m_lo >= 0) && (off + m_hi < LBA))
+                    window_sums<FULL>(bands + q * LBA + off, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
+                else
+                    window_sums<FULL>(delta + (size_t)(j0 + q) * a.Nt + r.n0, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
+                const float inv2R = 0.5f / R;
+                kA.add(s1 * inv2R);
+                if (FULL) {
+                    const float wA = Ai * inv2R;
+                    const float invR = 1.f / R;
+                    const float gR = wA * (s0 - s2 / (sig * sig)) - wA * s1 * invR;
+                    kX.add(gR * (r.v0x + dx) * invR);
+                    kY.add(gR * (r.v0y + dy) * invR);
+                    kZ.add(gR * (r.v0z + dz) * invR);
+                    kS.add(wA * s3 / (sig * sig * sig));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        gA[i] = kA.s;
+        if (FULL) {
+            if (gc) {
+                gc[i] = kX.s;
+                gc[g.M + i] = kY.s;
+                gc[2 * g.M + i] = kZ.s;
+            }
+            if (gs) gs[i] = kS.s;
+        }
+    }
+}
+
+int adj_band_len(float rad, float smax, float k, float invDelta) {
+    int half = (int)ceilf((rad + k * smax) * invDelta) + 4;
+    int lb = 2 * half + 8;
+    return (lb + 3) & ~3;
+}
+
+cudaError_t launch_adjoint(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const float* delta, float* gA,
+                           float* gc, float* gs, int LBA, cudaStream_t st) {
+    const bool full = gc != nullptr || gs != nullptr;
+    size_t smem = (size_t)ADJ_SC * LBA * sizeof(float);
+    unsigned blocks = (unsigned)g.ntiles;
+    cudaError_t e = cudaSuccess;
+#define GP_LAUNCH_ADJ(G, F)                                                                                   \
+    do {                                                                                                      \
+        e = cudaFuncSetAttribute(adj_kernel<G, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        if (e != cudaSuccess) return e;                                                                       \
+        adj_kernel<G, F><<<blocks, ADJ_THREADS, smem, st>>>(g, a, ti, delta, gA, gc, gs, LBA);               \
+    } while (0)
+    if (g.grid) {
+        if (full) GP_LAUNCH_ADJ(true, true); else GP_LAUNCH_ADJ(true, false);
+    } else {
+        if (full) GP_LAUNCH_ADJ(false, true); else GP_LAUNCH_ADJ(false, false);
+    }
+#undef GP_LAUNCH_ADJ
+    return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,483 @@
+// forward.cu -- the forward operator y = A(x) by direct windowed evaluation
+// (Methods, Eq. single_forward; the pair enumeration over |d| <= k sigma).
+//
+// Work decomposition.  Gaussians are cut into tiles (grid: 8x8x4 bricks, each loaded by one 3-D
+// TMA copy; SoA: 256 consecutive Gaussians) and tiles into slabs (grid: compact blocks of
+// bricks; SoA: contiguous tile ranges).  One CTA owns (slab, group of 8 sensors); each warp owns
+// one sensor.  For every tile the warp's lanes take Gaussians, evaluate each pair's window and add
+// the samples into a short per-tile float band with shared-memory atomics; the tile band is then
+// added into the slab's FP64 band, so long sums never accumulate in FP32.  The slab band is
+// flushed once into a per-slab partial signal (coalesced stores; grid mode stores only the band
+// and its offset), and a second kernel sums the slabs in a fixed order.  No global atomics.
+#include <cuda.h>
+
+#include <cstring>
+
+#include "gpair_internal.cuh"
+
+namespace gp {
+
+constexpr int FWD_SPC = 8;        // sensors per CTA (one per warp)
+constexpr int FWD_THREADS = 256;
+
+// ------------------------------------------------------------------------------------------
+// Tile summaries.  Grid mode: analytic (reference = brick centre).  SoA mode: bounding box of
+// the tile's Gaussians; the reference is the box centre rounded to float.
+
+__global__ void tile_info_grid_kernel(GaussDev g, TileInfo* ti) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= g.ntiles) return;
+    int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
+    TileInfo r;
+    r.c0x = (float)(g.ox + (tx * BX + BX / 2) * (double)g.h);   // informational in grid mode
+    r.c0y = (float)(g.oy + (ty * BY + BY / 2) * (double)g.h);
+    r.c0z = (float)(g.oz + (tz * BZ + BZ / 2) * (double)g.h);
+    r.rad = brick_radius(g.h);
+    r.smax = g.sigma;
+    int cx = min(BX, g.nx - tx * BX), cy = min(BY, g.ny - ty * BY), cz = min(BZ, g.nz - tz * BZ);
+    r.count = cx * cy * cz;
+    r.pad0 = r.pad1 = 0;
+    ti[t] = r;
+}
+
+__global__ void __launch_bounds__(TILE) tile_info_soa_kernel(GaussDev g, TileInfo* ti) {
+    __shared__ float red[7][TILE / 32];
+    __shared__ float s_c0[3];
+    const int64_t t = blockIdx.x;
+    const int64_t i = t * TILE + threadIdx.x;
+    const bool ok = i < g.M;
+    const float x = ok ? g.cx[i] : 0.f, y = ok ? g.cy[i] : 0.f, z = ok ? g.cz[i] : 0.f;
+    float v[7] = {ok ? x : 3e38f, ok ? y : 3e38f, ok ? z : 3e38f, ok ? -x : 3e38f, ok ? -y : 3e38f,
+                  ok ? -z : 3e38f, ok ? -g.sg[i] : 3e38f};
+    for (int q = 0; q < 7; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] = fminf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) for (int q = 0; q < 7; ++q) red[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b[7];
+        for (int q = 0; q < 7; ++q) { b[q] = red[q][0]; for (int k = 1; k < TILE / 32; ++k) b[q] = fminf(b[q], red[q][k]); }
+        s_c0[0] = 0.5f * (b[0] - b[3]); s_c0[1] = 0.5f * (b[1] - b[4]); s_c0[2] = 0.5f * (b[2] - b[5]);
+        red[0][0] = -b[6];
+    }
+    __syncthreads();
+    const float c0x = s_c0[0], c0y = s_c0[1], c0z = s_c0[2], smax = red[0][0];
+    const float dx = x - c0x, dy = y - c0y, dz = z - c0z;
+    float r2 = ok ? dx * dx + dy * dy + dz * dz : 0.f;
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    __syncthreads();
+    if (lane == 0) red[1][w] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = red[1][0];
+        for (int k = 1; k < TILE / 32; ++k) m = fmaxf(m, red[1][k]);
+        TileInfo r;
+        r.c0x = c0x; r.c0y = c0y; r.c0z = c0z;
+        r.rad = sqrtf(m) * 1.0001f + 1e-9f;
+        r.smax = smax;
+        int64_t cnt = g.M - t * TILE;
+        r.count = (int)(cnt > TILE ? TILE : cnt);
+        r.pad0 = r.pad1 = 0;
+        ti[t] = r;
+    }
+}
+
+// Grid mode: slab s is block (sx, sy, sz) of the block lattice; its bounding box is the box of
+// its node centres.
+__global__ void slab_info_grid_kernel(GaussDev g, int sbx, int sby, int sbz, int nsx, int nsy, int S,
+                                      SlabInfo* si) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int sx = s % nsx, sy = (s / nsx) % nsy, sz = s / (nsx * nsy);
+    SlabInfo o;
+    o.bx0 = sx * sbx; o.by0 = sy * sby; o.bz0 = sz * sbz;
+    o.bdx = min(sbx, g.ntx - o.bx0); o.bdy = min(sby, g.nty - o.by0); o.bdz = min(sbz, g.ntz - o.bz0);
+    const int ax = o.bx0 * BX, bxn = min(g.nx, (o.bx0 + o.bdx) * BX);
+    const int ay = o.by0 * BY, byn = min(g.ny, (o.by0 + o.bdy) * BY);
+    const int az = o.bz0 * BZ, bzn = min(g.nz, (o.bz0 + o.bdz) * BZ);
+    o.lo[0] = (float)(g.ox + (ax + 0.5) * g.h); o.hi[0] = (float)(g.ox + (bxn - 0.5) * g.h);
+    o.lo[1] = (float)(g.oy + (ay + 0.5) * g.h); o.hi[1] = (float)(g.oy + (byn - 0.5) * g.h);
+    o.lo[2] = (float)(g.oz + (az + 0.5) * g.h); o.hi[2] = (float)(g.oz + (bzn - 0.5) * g.h);
+    // widen by a few ulp so that float rounding of the box never cuts a centre off
+    for (int q = 0; q < 3; ++q) {
+        float pad = 1e-6f * (fabsf(o.lo[q]) + fabsf(o.hi[q])) + 1e-9f;
+        o.lo[q] -= pad; o.hi[q] += pad;
+    }
+    o.smax = g.sigma;
+    o.t_begin = 0; o.t_end = o.bdx * o.bdy * o.bdz;
+    o.pad = 0;
+    si[s] = o;
+}
+
+// SoA mode: bounding box (reference +- radius) and widest sigma of each contiguous tile range.
+__global__ void slab_info_soa_kernel(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, SlabInfo* si) {
+    __shared__ float red[7][FWD_THREADS / 32];
+    const int s = blockIdx.x;
+    int64_t tb = s * tiles_per_slab, te = tb + tiles_per_slab;
+    if (te > ntiles) te = ntiles;
+    float v[7] = {3e38f, 3e38f, 3e38f, 3e38f, 3e38f, 3e38f, 0.f};
+    for (int64_t t = tb + threadIdx.x; t < te; t += blockDim.x) {
+        TileInfo r = ti[t];
+        v[0] = fminf(v[0], r.c0x - r.rad); v[1] = fminf(v[1], r.c0y - r.rad); v[2] = fminf(v[2], r.c0z - r.rad);
+        v[3] = fminf(v[3], -(r.c0x + r.rad)); v[4] = fminf(v[4], -(r.c0y + r.rad)); v[5] = fminf(v[5], -(r.c0z + r.rad));
+        v[6] = fmaxf(v[6], r.smax);
+    }
+    for (int q = 0; q < 6; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] = fminf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    for (int o = 16; o > 0; o >>= 1) v[6] = fmaxf(v[6], __shfl_xor_sync(0xffffffffu, v[6], o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) for (int q = 0; q < 7; ++q) red[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        SlabInfo o;
+        for (int q = 0; q < 3; ++q) {
+            float a = red[q][0], b = red[q + 3][0];
+            for (int k = 1; k < nw; ++k) { a = fminf(a, red[q][k]); b = fminf(b, red[q + 3][k]); }
+            o.lo[q] = a; o.hi[q] = -b;
+        }
+        float sm = red[6][0];
+        for (int k = 1; k < nw; ++k) sm = fmaxf(sm, red[6][k]);
+        o.smax = sm;
+        o.t_begin = (int)tb; o.t_end = (int)te;
+        o.bx0 = o.by0 = o.bz0 = 0; o.bdx = o.bdy = o.bdz = 0; o.pad = 0;
+        si[s] = o;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward slab kernel.
+
+struct FwdSmem {
+    float tile[2][5][TILE];   // [buffer][A, cx, cy, cz, sigma][Gaussian]; grid mode uses A only
+    uint64_t mbar[2];
+    int npass;
+    int abort;
+};
+// Bands follow the header at a 128-byte boundary: per warp a float tile band of TB entries,
+// then per warp an FP64 slab band of LB entries.
+constexpr size_t FWD_HDR = (sizeof(FwdSmem) + 127) & ~(size_t)127;
+
+__device__ __forceinline__ void box_distance(const SlabInfo& sl, float sx, float sy, float sz,
+                                             double& dmin, double& dmax) {
+    double s[3] = {sx, sy, sz}, mn = 0, mx = 0;
+    for (int q = 0; q < 3; ++q) {
+        double lo = sl.lo[q], hi = sl.hi[q];
+        double a = lo - s[q], b = s[q] - hi;
+        double out = a > 0 ? a : (b > 0 ? b : 0.0);
+        mn += out * out;
+        double far = fabs(s[q] - lo) > fabs(s[q] - hi) ? fabs(s[q] - lo) : fabs(s[q] - hi);
+        mx += far * far;
+    }
+    dmin = sqrt(mn);
+    dmax = sqrt(mx);
+}
+
+// Tile t (0-based within the slab) -> brick coordinates (grid mode).
+__device__ __forceinline__ void slab_brick(const SlabInfo& sl, int t, int& tx, int& ty, int& tz) {
+    tx = sl.bx0 + t % sl.bdx;
+    ty = sl.by0 + (t / sl.bdx) % sl.bdy;
+    tz = sl.bz0 + t / (sl.bdx * sl.bdy);
+}
+
+// banded = 1 (grid mode): the partial row of (slab, sensor) holds only the slab's band window,
+// at offset rows[].x, length rows[].y; PL = LB.  banded = 0: full rows of PL = N_t samples,
+// written completely (zeros outside the band).
+template <bool GRID>
+__global__ void __launch_bounds__(FWD_THREADS)
+fwd_slab_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const SlabInfo* __restrict__ slabs,
+                float* __restrict__ partial, int2* __restrict__ rows, int PL, int LB, int TB, int banded,
+                int* status, int use_tma, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+    float* tbands = reinterpret_cast<float*>(smem_raw + FWD_HDR);
+    double* lbands = reinterpret_cast<double*>(smem_raw + FWD_HDR + (((size_t)FWD_SPC * TB * 4 + 127) & ~(size_t)127));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slab = blockIdx.y;
+    const int j = blockIdx.x * FWD_SPC + warp;
+    const bool has_sensor = j < a.Nd;
+    const SlabInfo sl = slabs[slab];
+    const int nTiles = sl.t_end - sl.t_begin;
+    float* tband = tbands + (size_t)warp * TB;
+    double* lband = lbands + (size_t)warp * LB;
+    const size_t row = (size_t)slab * a.Nd + (has_sensor ? j : 0);
+    float* prow = partial + row * PL;
+
+    // Band of samples this (slab, sensor) can touch.
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int n_lo = 0, n_hi = -1;
+    if (has_sensor) {
+        sx = a.xyz[3 * j]; sy = a.xyz[3 * j + 1]; sz = a.xyz[3 * j + 2];
+        if (nTiles > 0) {
+            double dmin, dmax;
+            box_distance(sl, sx, sy, sz, dmin, dmax);
+            double ks = (double)a.k * sl.smax;
+            double lo = floor(((dmin - ks) / a.v - a.t0) * a.fs) - 2.0;
+            double hi = ceil(((dmax + ks) / a.v - a.t0) * a.fs) + 2.0;
+            if (lo < 0) lo = 0;
+            if (hi > a.Nt - 1) hi = a.Nt - 1;
+            if (lo <= hi) { n_lo = (int)lo; n_hi = (int)hi; }
+        }
+    }
+    const int wa = n_lo & ~3;
+    int npass_j = (n_lo <= n_hi) ? (n_hi + 1 - wa + LB - 1) / LB : 0;
+    if (banded && npass_j > 1) {      // cannot happen with the host's band bound; keep memory safe
+        set_status(status, DEV_CAPACITY);
+        npass_j = 1;
+    }
+    if (threadIdx.x == 0) { S.npass = 0; S.abort = 0; }
+    __syncthreads();
+    if (lane == 0 && has_sensor) {
+        atomicMax(&S.npass, npass_j);
+        if (banded) rows[row] = make_int2(wa, npass_j > 0 ? min(LB, a.Nt - wa) : 0);
+    }
+
+    // Full-row mode: zero the partial row outside the windows the passes will write.
+    if (has_sensor && !banded) {
+        int wend = (npass_j > 0) ? min(a.Nt, wa + npass_j * LB) : 0;
+        int zb = (npass_j > 0) ? wa : a.Nt;
+        for (int n = lane; n < zb; n += 32) prow[n] = 0.f;
+        for (int n = wend + lane; n < a.Nt; n += 32) prow[n] = 0.f;
+    }
+    const bool tma = GRID && use_tma;
+    if (tma && threadIdx.x == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int npass = S.npass;
+    const int64_t total = (int64_t)npass * nTiles;
+
+    auto issue = [&](int64_t T) {
+        // grid mode: one 3-D TMA box (8 x 8 x 4 floats of A) per tile
+        int tx, ty, tz;
+        slab_brick(sl, (int)(T % nTiles), tx, ty, tz);
+        const int b = (int)(T & 1);
+        mbar_arrive_expect_tx(&S.mbar[b], TILE * sizeof(float));
+        tma_load_3d(&S.tile[b][0][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.mbar[b]);
+    };
+    if (tma && threadIdx.x == 0) {
+        if (total > 0) issue(0);
+        if (total > 1) issue(1);
+    }
+
+    const float Delta = a.Delta, invDelta = a.invDelta;
+    const float c2g = GRID ? -0.72134752044448170368f / (g.sigma * g.sigma) : 0.f;  // -log2(e)/2/s^2
+    const float reach_g = GRID ? brick_radius(g.h) + a.k * g.sigma : 0.f;
+
+    int64_t T = 0;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int w = wa + pass * LB;
+        const bool active = has_sensor && pass < npass_j;
+        for (int q = lane; q < LB; q += 32) lband[q] = 0.0;
+        __syncwarp();
+        PairRef refs;            // lane q holds the reference of tile (t & ~31) + q
+        for (int t = 0; t < nTiles; ++t, ++T) {
+            const int b = (int)(T & 1);
+            if (tma) {
+                bool ok = mbar_wait(&S.mbar[b], (uint32_t)((T >> 1) & 1));
+                if (!ok) S.abort = 1;
+                __syncthreads();
+                if (S.abort) goto aborted;
+            } else if (GRID) {
+                // brick without a TMA descriptor (row pitch not 16-byte aligned): plain loads
+                int tx, ty, tz;
+                slab_brick(sl, t, tx, ty, tz);
+                for (int q = threadIdx.x; q < TILE; q += FWD_THREADS) {
+                    const int gx = tx * BX + (q & (BX - 1)), gy = ty * BY + ((q / BX) & (BY - 1)), gz = tz * BZ + q / (BX * BY);
+                    const bool ok = gx < g.nx && gy < g.ny && gz < g.nz;
+                    S.tile[b][0][q] = ok ? g.A[((int64_t)gz * g.ny + gy) * g.nx + gx] : 0.f;
+                }
+                __syncthreads();
+            } else {
+                const int64_t base = (int64_t)(sl.t_begin + t) * TILE;
+                for (int q = threadIdx.x; q < TILE; q += FWD_THREADS) {
+                    int64_t i = base + q;
+                    bool ok = i < g.M;
+                    S.tile[b][0][q] = ok ? g.A[i] : 0.f;
+                    S.tile[b][1][q] = ok ? g.cx[i] : 0.f;
+                    S.tile[b][2][q] = ok ? g.cy[i] : 0.f;
+                    S.tile[b][3][q] = ok ? g.cz[i] : 0.f;
+                    S.tile[b][4][q] = ok ? g.sg[i] : 1.f;
+                }
+                __syncthreads();
+            }
+            if (active) {
+                if ((t & 31) == 0 && t + lane < nTiles) {
+                    if (GRID) {
+                        int tx, ty, tz;
+                        slab_brick(sl, t + lane, tx, ty, tz);
+                        refs = make_ref(g.ox + (tx * BX + BX / 2) * (double)g.h, g.oy + (ty * BY + BY / 2) * (double)g.h,
+                                        g.oz + (tz * BZ + BZ / 2) * (double)g.h, sx, sy, sz, a);
+                    } else {
+                        const TileInfo r = ti[sl.t_begin + t + lane];
+                        refs = make_ref(r.c0x, r.c0y, r.c0z, sx, sy, sz, a);
+                    }
+                }
+                const int src = t & 31;
+                PairRef r;
+                r.v0x = __shfl_sync(0xffffffffu, refs.v0x, src);
+                r.v0y = __shfl_sync(0xffffffffu, refs.v0y, src);
+                r.v0z = __shfl_sync(0xffffffffu, refs.v0z, src);
+                r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
+                r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
+                r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
+                float rc0x = 0.f, rc0y = 0.f, rc0z = 0.f, reach = reach_g;
+                if (!GRID) {
+                    const TileInfo rt = ti[sl.t_begin + t];
+                    rc0x = rt.c0x; rc0y = rt.c0y; rc0z = rt.c0z;
+                    reach = rt.rad + a.k * rt.smax;
+                }
+                // samples this tile can touch, inside this pass's window and the record
+                int ta = r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2;
+                int tb = r.n0 + (int)ceilf((r.phi0 + reach) * invDelta) + 2;
+                ta = max(ta, max(w, 0));
+                tb = min(tb, min(w + LB - 1, a.Nt - 1));
+                for (int sw = ta; sw <= tb; sw += TB) {
+                    const int se = min(sw + TB - 1, tb);
+                    for (int q = lane; q < TB; q += 32) tband[q] = 0.f;
+                    __syncwarp();
+                    const int mlo_cap = sw - r.n0, mhi_cap = se - r.n0;
+                    const int bofs = r.n0 - sw;
+                    for (int l = lane; l < TILE; l += 32) {
+                        const float Ai = S.tile[b][0][l];
+                        if (Ai == 0.f) continue;
+                        float dx, dy, dz, sig, c2;
+                        if (GRID) {
+                            brick_offset(l, g.h, dx, dy, dz);
+                            sig = g.sigma;
+                            c2 = c2g;
+                        } else {
+                            dx = S.tile[b][1][l] - rc0x;
+                            dy = S.tile[b][2][l] - rc0y;
+                            dz = S.tile[b][3][l] - rc0z;
+                            sig = S.tile[b][4][l];
+                            c2 = -0.72134752044448170368f / (sig * sig);
+                        }
+                        float R, phi;
+                        pair_phase(r, dx, dy, dz, R, phi);
+                        const float ks = a.k * sig;
+                        const int m_lo = max((int)ceilf((phi - ks) * invDelta), mlo_cap);
+                        const int m_hi = min((int)floorf((phi + ks) * invDelta), mhi_cap);
+                        const float wgt = Ai * 0.5f / R;
+                        for (int m = m_lo; m <= m_hi; ++m) {
+                            const float d = fmaf(-(float)m, Delta, phi);
+                            const float e = ex2_approx(d * d * c2);
+                            atomicAdd(&tband[bofs + m], wgt * d * e);
+                        }
+                    }
+                    __syncwarp();
+                    for (int q = lane; q <= se - sw; q += 32) lband[sw - w + q] += (double)tband[q];
+                    __syncwarp();
+                }
+            }
+            __syncthreads();   // every warp is done with buffer b
+            if (tma && threadIdx.x == 0 && T + 2 < total) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(T + 2);
+            }
+        }
+        __syncwarp();
+        if (active) {
+            const int wend = min(a.Nt, w + LB);
+            float* dst = banded ? prow : prow + w;
+            for (int q = lane; q < wend - w; q += 32) dst[q] = (float)lband[q];
+        }
+        __syncwarp();
+    }
+    return;
+aborted:
+    set_status(status, DEV_TIMEOUT);
+    // Let the copies this CTA issued land before its shared memory is released.
+    if (tma && threadIdx.x == 0) {
+        for (int64_t U = T; U < total && U < T + 2; ++U) mbar_wait(&S.mbar[U & 1], (uint32_t)((U >> 1) & 1));
+    }
+}
+
+// y[j][n] = sum over slabs of the partial rows, fixed slab order.  Banded rows cover
+// [rows.x, rows.x + rows.y); full rows (banded = 0) cover the whole record.
+__global__ void slab_reduce_kernel(const float* __restrict__ partial, const int2* __restrict__ rows, int S, int Nd,
+                                   int Nt, int PL, int banded, float* __restrict__ y) {
+    const int j = blockIdx.y;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < Nt; n += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int s = 0; s < S; ++s) {
+            const size_t r = (size_t)s * Nd + j;
+            if (banded) {
+                const int2 ri = rows[r];
+                const int q = n - ri.x;
+                if (q >= 0 && q < ri.y) acc += partial[r * PL + q];
+            } else {
+                acc += partial[r * PL + n];
+            }
+        }
+        y[(size_t)j * Nt + n] = acc;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host side.
+
+size_t fwd_smem_bytes(int LB, int TB) {
+    return FWD_HDR + (((size_t)FWD_SPC * TB * 4 + 127) & ~(size_t)127) + (size_t)FWD_SPC * LB * 8;
+}
+
+static const CUtensorMap& null_tmap() {
+    static CUtensorMap m = [] { CUtensorMap z; memset(&z, 0, sizeof(z)); return z; }();
+    return m;
+}
+
+cudaError_t launch_tile_info(const GaussDev& g, TileInfo* ti, cudaStream_t st) {
+    if (g.grid) {
+        int blocks = (int)((g.ntiles + 255) / 256);
+        tile_info_grid_kernel<<<blocks, 256, 0, st>>>(g, ti);
+    } else {
+        tile_info_soa_kernel<<<(unsigned)g.ntiles, TILE, 0, st>>>(g, ti);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_info_grid(const GaussDev& g, int sbx, int sby, int sbz, int S, SlabInfo* si,
+                                  cudaStream_t st) {
+    const int nsx = (g.ntx + sbx - 1) / sbx, nsy = (g.nty + sby - 1) / sby;
+    slab_info_grid_kernel<<<(S + 127) / 128, 128, 0, st>>>(g, sbx, sby, sbz, nsx, nsy, S, si);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
+                                 cudaStream_t st) {
+    slab_info_soa_kernel<<<S, FWD_THREADS, 0, st>>>(ti, ntiles, tiles_per_slab, si);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
+                           float* partial, int2* rows, int PL, int LB, int TB, int* status,
+                           const CUtensorMap* tmap, cudaStream_t st) {
+    const size_t smem = fwd_smem_bytes(LB, TB);
+    const int banded = g.grid ? 1 : 0;
+    dim3 grid((a.Nd + FWD_SPC - 1) / FWD_SPC, S);
+    cudaError_t e;
+    if (g.grid) {
+        e = cudaFuncSetAttribute(fwd_slab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fwd_slab_kernel<true><<<grid, FWD_THREADS, smem, st>>>(g, a, ti, si, partial, rows, PL, LB, TB, banded, status,
+                                                               tmap != nullptr, *(tmap ? tmap : &null_tmap()));
+    } else {
+        e = cudaFuncSetAttribute(fwd_slab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fwd_slab_kernel<false><<<grid, FWD_THREADS, smem, st>>>(g, a, ti, si, partial, rows, PL, LB, TB, banded,
+                                                                status, 0, null_tmap());
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
+                               int PL, float* y, cudaStream_t st) {
+    dim3 rgrid((a.Nt + 255) / 256, a.Nd);
+    slab_reduce_kernel<<<rgrid, 256, 0, st>>>(partial, rows, S, a.Nd, a.Nt, PL, g.grid ? 1 : 0, y);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,599 @@
+// gpair_abi.cu -- the C ABI declared in include/gpair.h: argument validation, the per-stream
+// scratch pool, TMA descriptor set-up, launch configuration and the reconstruction solver.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "gpair_internal.cuh"
+
+namespace gp {
+cudaError_t launch_tile_info(const GaussDev& g, TileInfo* ti, cudaStream_t st);
+cudaError_t launch_slab_info_grid(const GaussDev& g, int sbx, int sby, int sbz, int S, SlabInfo* si, cudaStream_t st);
+cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
+                                 cudaStream_t st);
+cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
+                           float* partial, int2* rows, int PL, int LB, int TB, int* status,
+                           const CUtensorMap* tmap, cudaStream_t st);
+cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
+                               int PL, float* y, cudaStream_t st);
+int adj_band_len(float rad, float smax, float k, float invDelta);
+cudaError_t launch_adjoint(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const float* delta, float* gA,
+                           float* gc, float* gs, int LBA, cudaStream_t st);
+cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
+cudaError_t launch_resid(const float* y, const float* b, float* delta, float scale, int64_t n, double* partial,
+                         double* out, cudaStream_t st);
+cudaError_t launch_reduce2(const float* a, const float* b, const float* c, int64_t n, double* partial, double* out,
+                           cudaStream_t st);
+cudaError_t launch_ls(const float* r, const float* Fg, int64_t n, float* x, const float* g, int64_t M,
+                      double* partial, double* nd, cudaStream_t st);
+cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float eta,
+                        float b1, float b2, float inv_c1, float inv_sqrt_c2, float adam_eps, cudaStream_t st);
+int red_blocks();
+bool vox_is_lattice(const GaussDev& g, const gpair_grid& og);
+cudaError_t launch_voxelize(const GaussDev& g, const gpair_grid& og, float k, float* vol, float* tmp, cudaStream_t st);
+}  // namespace gp
+
+using namespace gp;
+
+namespace {
+
+constexpr int SPC = 8;            // sensors per forward CTA (matches the kernel)
+constexpr int SM_COUNT_HINT = 152;
+
+// ---- per-(device, stream) scratch pool -------------------------------------------------
+
+struct Scratch {
+    void* buf = nullptr;
+    size_t cap = 0;
+    int* status = nullptr;        // device status word
+};
+
+std::mutex g_pool_mu;
+std::unordered_map<uint64_t, Scratch> g_pool;
+
+uint64_t pool_key(int dev, cudaStream_t st) { return ((uint64_t)(uint32_t)dev << 48) ^ (uint64_t)(uintptr_t)st; }
+
+gpair_status get_scratch(cudaStream_t st, size_t bytes, void** out_buf, int** out_status) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GPAIR_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    Scratch& s = g_pool[pool_key(dev, st)];
+    if (!s.status) {
+        if (cudaMalloc(&s.status, sizeof(int)) != cudaSuccess) { s.status = nullptr; return GPAIR_ERR_NOMEM; }
+        if (cudaMemsetAsync(s.status, 0, sizeof(int), st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    }
+    if (s.cap < bytes) {
+        if (s.buf) {
+            cudaStreamSynchronize(st);
+            cudaFree(s.buf);
+            s.buf = nullptr;
+            s.cap = 0;
+        }
+        size_t want = bytes + bytes / 8 + 4096;
+        if (cudaMalloc(&s.buf, want) != cudaSuccess) { s.buf = nullptr; cudaGetLastError(); return GPAIR_ERR_NOMEM; }
+        s.cap = want;
+    }
+    if (out_buf) *out_buf = s.buf;
+    if (out_status) *out_status = s.status;
+    return GPAIR_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- argument conversion ------------------------------------------------------------------
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+
+gpair_status make_gauss(const gpair_gaussians* gi, GaussDev& g) {
+    if (!gi || gi->M <= 0 || !gi->A) return GPAIR_ERR_INVALID_ARG;
+    memset(&g, 0, sizeof(g));
+    g.M = gi->M;
+    g.A = gi->A;
+    if (!gi->cx) {
+        const gpair_grid* gr = gi->grid;
+        if (!gr || gr->nx <= 0 || gr->ny <= 0 || gr->nz <= 0) return GPAIR_ERR_INVALID_ARG;
+        if ((int64_t)gr->nx * gr->ny * gr->nz != gi->M) return GPAIR_ERR_INVALID_ARG;
+        if (!finite_pos(gr->dx) || !finite_pos(gr->sigma)) return GPAIR_ERR_INVALID_ARG;
+        if (!std::isfinite(gr->ox) || !std::isfinite(gr->oy) || !std::isfinite(gr->oz)) return GPAIR_ERR_INVALID_ARG;
+        g.grid = 1;
+        g.nx = gr->nx; g.ny = gr->ny; g.nz = gr->nz;
+        g.h = gr->dx; g.sigma = gr->sigma;
+        g.ox = gr->ox; g.oy = gr->oy; g.oz = gr->oz;
+        g.ntx = (gr->nx + BX - 1) / BX; g.nty = (gr->ny + BY - 1) / BY; g.ntz = (gr->nz + BZ - 1) / BZ;
+        g.ntiles = (int64_t)g.ntx * g.nty * g.ntz;
+    } else {
+        if (!gi->cy || !gi->cz || !gi->sigma) return GPAIR_ERR_INVALID_ARG;
+        g.grid = 0;
+        g.cx = gi->cx; g.cy = gi->cy; g.cz = gi->cz; g.sg = gi->sigma;
+        g.ntiles = (gi->M + TILE - 1) / TILE;
+    }
+    if (g.ntiles > (int64_t)INT32_MAX) return GPAIR_ERR_UNSUPPORTED;
+    return GPAIR_OK;
+}
+
+gpair_status make_arr(const gpair_array* ai, ArrDev& a) {
+    if (!ai || ai->n_sensors <= 0 || !ai->xyz || ai->n_samples <= 0) return GPAIR_ERR_INVALID_ARG;
+    if (ai->n_samples > (1 << 27) || ai->n_sensors > 65535) return GPAIR_ERR_UNSUPPORTED;
+    if (!finite_pos(ai->sound_speed) || !finite_pos(ai->fs) || !finite_pos(ai->window_k)) return GPAIR_ERR_INVALID_ARG;
+    if (!std::isfinite(ai->t0)) return GPAIR_ERR_INVALID_ARG;
+    a.Nd = ai->n_sensors;
+    a.xyz = ai->xyz;
+    a.v = ai->sound_speed;
+    a.fs = ai->fs;
+    a.t0 = ai->t0;
+    a.Nt = ai->n_samples;
+    a.k = ai->window_k;
+    a.Delta = (float)((double)ai->sound_speed / (double)ai->fs);
+    a.invDelta = (float)((double)ai->fs / (double)ai->sound_speed);
+    return GPAIR_OK;
+}
+
+// ---- TMA descriptor for the grid amplitude volume ------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map over A[nz][ny][nx] float32 with an 8 x 8 x 4 box; out-of-range elements read as 0.
+bool make_tmap(const GaussDev& g, CUtensorMap* map) {
+    if (((uintptr_t)g.A & 15) != 0 || (g.nx % 4) != 0) return false;
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4};
+    cuuint32_t box[3] = {BX, BY, BZ};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(g.A), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+gpair_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GPAIR_OK;
+    if (e == cudaErrorMemoryAllocation) return GPAIR_ERR_NOMEM;
+    if (e == cudaErrorInvalidValue) return GPAIR_ERR_UNSUPPORTED;
+    return GPAIR_ERR_CUDA;
+}
+
+// ---- forward plan ---------------------------------------------------------------------------
+
+struct FwdPlan {
+    int S;                 // slabs
+    int64_t tiles_per_slab;        // SoA mode
+    int sbx, sby, sbz;     // grid mode: slab block size in bricks
+    int LB;                // slab band entries per sensor (FP64 in shared memory)
+    int TB;                // tile band entries per sensor (float, atomics)
+    int PL;                // partial row length
+    size_t off_ti, off_si, off_rows, off_part, bytes;
+};
+
+FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
+    FwdPlan p;
+    memset(&p, 0, sizeof(p));
+    const int ngroups = (a.Nd + SPC - 1) / SPC;
+    const int64_t target_S = ((int64_t)SM_COUNT_HINT * 4 * 4 + ngroups - 1) / ngroups;
+    if (g.grid) {
+        // Compact blocks of bricks: start from 8 x 8 x 8 bricks and halve the longest side until
+        // there are enough CTAs; the band of a block is bounded by its diagonal.
+        int sb[3] = {std::min(8, g.ntx), std::min(8, g.nty), std::min(8, g.ntz)};
+        const int nt[3] = {g.ntx, g.nty, g.ntz};
+        const double ext[3] = {BX * (double)g.h, BY * (double)g.h, BZ * (double)g.h};
+        auto count = [&] {
+            int64_t s = 1;
+            for (int q = 0; q < 3; ++q) s *= (nt[q] + sb[q] - 1) / sb[q];
+            return s;
+        };
+        while (count() < target_S) {
+            int best = -1;
+            double len = 0;
+            for (int q = 0; q < 3; ++q)
+                if (sb[q] > 1 && sb[q] * ext[q] > len) { len = sb[q] * ext[q]; best = q; }
+            if (best < 0) break;
+            sb[best] = (sb[best] + 1) / 2;
+        }
+        p.sbx = sb[0]; p.sby = sb[1]; p.sbz = sb[2];
+        p.S = (int)count();
+        const double dx = sb[0] * ext[0], dy = sb[1] * ext[1], dz = sb[2] * ext[2];
+        const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+        p.LB = ((int)std::ceil((diag + 2.0 * a.k * g.sigma) * a.invDelta) + 16 + 3) & ~3;
+        p.PL = p.LB;
+        const double reach = brick_radius(g.h) + a.k * g.sigma;
+        p.TB = ((int)std::ceil(2.0 * reach * a.invDelta) + 8 + 31) & ~31;
+        if (p.TB > 512) p.TB = 512;
+    } else {
+        int64_t S = target_S;
+        if (S > g.ntiles) S = g.ntiles;
+        const int64_t row = (int64_t)a.Nd * a.Nt * 4;
+        while (S > 1 && S * row > ((int64_t)2 << 30)) S = (S + 1) / 2;
+        if (S < 1) S = 1;
+        p.tiles_per_slab = (g.ntiles + S - 1) / S;
+        p.S = (int)((g.ntiles + p.tiles_per_slab - 1) / p.tiles_per_slab);
+        p.LB = std::min(512, ((a.Nt + 4) + 3) & ~3);
+        p.PL = a.Nt;
+        p.TB = 256;
+    }
+    p.off_ti = 0;
+    p.off_si = align256(sizeof(TileInfo) * (size_t)g.ntiles);
+    p.off_rows = p.off_si + align256(sizeof(SlabInfo) * (size_t)p.S);
+    p.off_part = p.off_rows + align256(sizeof(int2) * (size_t)p.S * a.Nd);
+    p.bytes = p.off_part + align256((size_t)p.S * a.Nd * p.PL * 4);
+    return p;
+}
+
+// ev (optional): two events recorded immediately before and after the slab kernel.
+gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStream_t st, void* scratch, int* status,
+                         const FwdPlan& p, const cudaEvent_t* ev = nullptr) {
+    char* base = static_cast<char*>(scratch);
+    TileInfo* ti = reinterpret_cast<TileInfo*>(base + p.off_ti);
+    SlabInfo* si = reinterpret_cast<SlabInfo*>(base + p.off_si);
+    int2* rows = reinterpret_cast<int2*>(base + p.off_rows);
+    float* part = reinterpret_cast<float*>(base + p.off_part);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    const bool tma = g.grid && make_tmap(g, &map);   // ragged row pitch: plain brick loads instead
+    cudaError_t e = cudaSuccess;
+    if (g.grid) {
+        e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
+    } else {
+        e = launch_tile_info(g, ti, st);
+        if (e == cudaSuccess) e = launch_slab_info_soa(ti, g.ntiles, p.tiles_per_slab, p.S, si, st);
+    }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess)
+        e = launch_forward(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.TB, status, tma ? &map : nullptr, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = launch_slab_reduce(g, a, part, rows, p.S, p.PL, y, st);
+    return cuda_status(e);
+}
+
+int adjoint_band(const GaussDev& g, const ArrDev& a) {
+    if (g.grid) return adj_band_len(brick_radius(g.h), g.sigma, a.k, a.invDelta);
+    return 256;
+}
+
+gpair_status run_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, float* gc, float* gs,
+                         cudaStream_t st, void* scratch, const cudaEvent_t* ev = nullptr) {
+    TileInfo* ti = static_cast<TileInfo*>(scratch);
+    cudaError_t e = launch_tile_info(g, ti, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_adjoint(g, a, ti, delta, gA, gc, gs, adjoint_band(g, a), st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+// ============================================================================================
+// Public entry points.
+
+extern "C" {
+
+const char* gpair_version(void) { return "gpair-gb300 0.1 (sm_103a)"; }
+
+const char* gpair_status_string(gpair_status s) {
+    switch (s) {
+        case GPAIR_OK: return "ok";
+        case GPAIR_ERR_INVALID_ARG: return "invalid argument";
+        case GPAIR_ERR_CUDA: return "CUDA error";
+        case GPAIR_ERR_NOMEM: return "out of device memory";
+        case GPAIR_ERR_TIMEOUT: return "device-side wait timed out";
+        case GPAIR_ERR_UNSUPPORTED: return "unsupported shape or layout";
+        case GPAIR_ERR_NONFINITE: return "non-finite input";
+    }
+    return "unknown status";
+}
+
+gpair_status gpair_forward(const gpair_gaussians* gi, const gpair_array* ai, float* y, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (!y) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FwdPlan p = plan_forward(g, a);
+    void* scratch = nullptr;
+    int* status = nullptr;
+    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    return run_forward(g, a, y, st, scratch, status, p);
+}
+
+gpair_status gpair_adjoint(const gpair_gaussians* gi, const gpair_array* ai, const float* delta, float* gA,
+                           float* gc, float* gsigma, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (!delta || !gA) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    if ((s = get_scratch(st, align256(sizeof(TileInfo) * (size_t)g.ntiles), &scratch, nullptr)) != GPAIR_OK) return s;
+    return run_adjoint(g, a, delta, gA, gc, gsigma, st, scratch);
+}
+
+gpair_status gpair_voxelize(const gpair_gaussians* gi, const gpair_grid* og, float window_k, float* vol,
+                            void* stream) {
+    GaussDev g;
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if (!og || !vol || og->nx <= 0 || og->ny <= 0 || og->nz <= 0 || !finite_pos(og->dx) || !finite_pos(window_k))
+        return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* tmp = nullptr;
+    if (vox_is_lattice(g, *og)) {
+        size_t bytes = (size_t)og->nx * og->ny * og->nz * 4;
+        if ((s = get_scratch(st, bytes, &tmp, nullptr)) != GPAIR_OK) return s;
+    }
+    return cuda_status(launch_voxelize(g, *og, window_k, vol, static_cast<float*>(tmp), st));
+}
+
+gpair_status gpair_reduce_f64(const float* a, const float* b, const float* c, int64_t n, double* out, void* stream) {
+    if (!a || !out || n <= 0) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    gpair_status s = get_scratch(st, sizeof(double) * 2 * red_blocks(), &scratch, nullptr);
+    if (s != GPAIR_OK) return s;
+    return cuda_status(launch_reduce2(a, b, c, n, static_cast<double*>(scratch), out, st));
+}
+
+gpair_status gpair_last_device_status(void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* status = nullptr;
+    gpair_status s = get_scratch(st, 0, nullptr, &status);
+    if (s != GPAIR_OK) return s;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (h == DEV_TIMEOUT) return GPAIR_ERR_TIMEOUT;
+    if (h == DEV_CAPACITY) return GPAIR_ERR_UNSUPPORTED;
+    return GPAIR_OK;
+}
+
+void gpair_release_scratch(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto it = g_pool.begin(); it != g_pool.end();) {
+        if ((it->first >> 48) == (uint64_t)(uint32_t)dev) {
+            cudaDeviceSynchronize();
+            if (it->second.buf) cudaFree(it->second.buf);
+            if (it->second.status) cudaFree(it->second.status);
+            it = g_pool.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Reconstruction solver (Algorithm 2).
+
+struct gpair_solver {
+    GaussDev g;              // A points at x (amplitudes of the current iterate)
+    ArrDev a;
+    gpair_step_params p;
+    int t = 0;
+    float *z = nullptr, *m = nullptr, *v = nullptr, *x = nullptr, *gx = nullptr;
+    float *y = nullptr, *delta = nullptr, *Fg = nullptr;
+    double* red = nullptr;   // reduction partials (2 * red_blocks) + results (4)
+    void* fwd_scratch = nullptr;
+    int* status = nullptr;
+    FwdPlan plan;
+    // Profiling (gpair_solver_profile): per recorded step six events on the step's stream --
+    // step start, forward slab kernel start/end, adjoint kernel start/end, step end.
+    bool prof = false;
+    std::vector<cudaEvent_t> evs;
+    int nrec = 0;
+};
+
+namespace {
+double cawr(int t, const gpair_step_params& p) {
+    // SGDR: periods T0, T0*Tmult, ...; T_cur counts iterations since the last restart.
+    double Tcur = t, Ti = p.T0 > 0 ? p.T0 : 1;
+    if (p.T_mult <= 1.0f) {
+        Tcur = std::fmod(Tcur, Ti);
+    } else {
+        while (Tcur >= Ti) { Tcur -= Ti; Ti *= p.T_mult; }
+    }
+    return p.eta_min + 0.5 * (p.eta_max - p.eta_min) * (1.0 + std::cos(M_PI * Tcur / Ti));
+}
+}  // namespace
+
+extern "C" {
+
+gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* ai, const gpair_step_params* prm,
+                                 gpair_solver** out) {
+    if (!out || !prm) return GPAIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    gpair_gaussians tmp = gi ? *gi : gpair_gaussians{};
+    static const float one = 1.f;
+    tmp.A = &one;   // amplitudes come from the solver; validate the rest
+    GaussDev g;
+    ArrDev a;
+    gpair_status s = make_gauss(&tmp, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (prm->rule != GPAIR_RULE_ADAM && prm->rule != GPAIR_RULE_GD_LINESEARCH) return GPAIR_ERR_INVALID_ARG;
+    if (prm->rule == GPAIR_RULE_ADAM &&
+        (!(prm->beta1 >= 0.f && prm->beta1 < 1.f) || !(prm->beta2 >= 0.f && prm->beta2 < 1.f) || !(prm->adam_eps >= 0.f)))
+        return GPAIR_ERR_INVALID_ARG;
+    gpair_solver* S = new gpair_solver();
+    S->g = g;
+    S->a = a;
+    S->p = *prm;
+    const size_t M = (size_t)g.M, N = (size_t)a.Nd * a.Nt;
+    S->plan = plan_forward(g, a);
+    bool ok = cudaMalloc(&S->z, M * 4) == cudaSuccess && cudaMalloc(&S->m, M * 4) == cudaSuccess &&
+              cudaMalloc(&S->v, M * 4) == cudaSuccess && cudaMalloc(&S->x, M * 4) == cudaSuccess &&
+              cudaMalloc(&S->gx, M * 4) == cudaSuccess && cudaMalloc(&S->y, N * 4) == cudaSuccess &&
+              cudaMalloc(&S->delta, N * 4) == cudaSuccess &&
+              (prm->rule != GPAIR_RULE_GD_LINESEARCH || cudaMalloc(&S->Fg, N * 4) == cudaSuccess) &&
+              cudaMalloc(&S->red, sizeof(double) * (2 * red_blocks() + 8)) == cudaSuccess &&
+              cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
+              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        gpair_solver_destroy(S);
+        return GPAIR_ERR_NOMEM;
+    }
+    cudaMemset(S->z, 0, M * 4);
+    cudaMemset(S->m, 0, M * 4);
+    cudaMemset(S->v, 0, M * 4);
+    cudaMemset(S->status, 0, sizeof(int));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        gpair_solver_destroy(S);
+        return GPAIR_ERR_CUDA;
+    }
+    S->g.A = S->x;
+    *out = S;
+    return GPAIR_OK;
+}
+
+void gpair_solver_destroy(gpair_solver* S) {
+    if (!S) return;
+    cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
+    cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
+    cudaFree(S->fwd_scratch); cudaFree(S->status);
+    for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
+    delete S;
+}
+
+gpair_status gpair_solver_profile(gpair_solver* S, int enable) {
+    if (!S) return GPAIR_ERR_INVALID_ARG;
+    S->prof = enable != 0;
+    S->nrec = 0;
+    return GPAIR_OK;
+}
+
+gpair_status gpair_solver_timings(gpair_solver* S, double* ms, int* nsteps) {
+    if (!S || !ms) return GPAIR_ERR_INVALID_ARG;
+    ms[0] = ms[1] = ms[2] = 0.0;
+    if (S->nrec > 0 && cudaEventSynchronize(S->evs[6 * S->nrec - 1]) != cudaSuccess) return GPAIR_ERR_CUDA;
+    for (int q = 0; q < S->nrec; ++q) {
+        const cudaEvent_t* e = &S->evs[6 * q];
+        float f = 0.f, a = 0.f, t = 0.f;
+        if (cudaEventElapsedTime(&f, e[1], e[2]) != cudaSuccess || cudaEventElapsedTime(&a, e[3], e[4]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e[0], e[5]) != cudaSuccess)
+            return GPAIR_ERR_CUDA;
+        ms[0] += f; ms[1] += a; ms[2] += t;
+    }
+    if (nsteps) *nsteps = S->nrec;
+    S->nrec = 0;
+    return GPAIR_OK;
+}
+
+gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, double* resid_out, void* stream) {
+    if (!S || !b) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t M = S->g.M, N = (int64_t)S->a.Nd * S->a.Nt;
+    double* partial = S->red;
+    double* res = S->red + 2 * red_blocks();
+    cudaError_t e;
+    gpair_status s;
+    void* adj_scratch = S->fwd_scratch;   // the adjoint needs only the tile summaries (same layout)
+    const cudaEvent_t* ev = nullptr;
+    if (S->prof) {
+        while ((int)S->evs.size() < 6 * (S->nrec + 1)) {
+            cudaEvent_t x;
+            if (cudaEventCreate(&x) != cudaSuccess) return GPAIR_ERR_CUDA;
+            S->evs.push_back(x);
+        }
+        ev = &S->evs[6 * S->nrec];
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    }
+    if (S->p.rule == GPAIR_RULE_ADAM) {
+        const int npc = S->p.npc != 0;
+        if ((e = launch_npc(S->z, S->x, M, npc, S->p.npc_eps, st)) != cudaSuccess) return cuda_status(e);
+        if ((s = run_forward(S->g, S->a, S->y, st, S->fwd_scratch, S->status, S->plan, ev ? ev + 1 : nullptr)) != GPAIR_OK)
+            return s;
+        if ((e = launch_resid(S->y, b, S->delta, (float)(2.0 / (double)N), N, partial, res, st)) != cudaSuccess)
+            return cuda_status(e);
+        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr)) !=
+            GPAIR_OK)
+            return s;
+        const int tt = S->t + 1;
+        const double c1 = 1.0 - std::pow((double)S->p.beta1, tt), c2 = 1.0 - std::pow((double)S->p.beta2, tt);
+        const float eta = (float)cawr(S->t, S->p);
+        if ((e = launch_adam(S->z, S->m, S->v, S->gx, M, npc, S->p.npc_eps, eta, S->p.beta1, S->p.beta2,
+                             (float)(1.0 / c1), (float)(1.0 / std::sqrt(c2)), S->p.adam_eps, st)) != cudaSuccess)
+            return cuda_status(e);
+    } else {
+        // steepest descent on x = z with the exact line search alpha = <r, F g> / |F g|^2
+        S->g.A = S->z;
+        if ((s = run_forward(S->g, S->a, S->y, st, S->fwd_scratch, S->status, S->plan, ev ? ev + 1 : nullptr)) != GPAIR_OK)
+            return s;
+        if ((e = launch_resid(S->y, b, S->delta, 1.0f, N, partial, res, st)) != cudaSuccess) return cuda_status(e);
+        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr)) !=
+            GPAIR_OK)
+            return s;
+        S->g.A = S->gx;
+        if ((s = run_forward(S->g, S->a, S->Fg, st, S->fwd_scratch, S->status, S->plan)) != GPAIR_OK) return s;
+        if ((e = launch_ls(S->delta, S->Fg, N, S->z, S->gx, M, partial, res + 2, st)) != cudaSuccess)
+            return cuda_status(e);
+        S->g.A = S->x;
+    }
+    if (ev) {
+        if (cudaEventRecord(ev[5], st) != cudaSuccess) return GPAIR_ERR_CUDA;
+        S->nrec += 1;
+    }
+    S->t += 1;
+    if (loss_out || resid_out) {
+        double h = 0.0;
+        if (cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
+        if (loss_out) *loss_out = h / (double)N;
+        if (resid_out) *resid_out = std::sqrt(h);
+    }
+    return GPAIR_OK;
+}
+
+gpair_status gpair_solver_image(gpair_solver* S, float* x_out, void* stream) {
+    if (!S || !x_out) return GPAIR_ERR_INVALID_ARG;
+    const int npc = S->p.rule == GPAIR_RULE_ADAM && S->p.npc != 0;
+    return cuda_status(launch_npc(S->z, x_out, S->g.M, npc, S->p.npc_eps, static_cast<cudaStream_t>(stream)));
+}
+
+gpair_status gpair_solver_get_state(gpair_solver* S, float* z, float* m, float* v, int* t, void* stream) {
+    if (!S) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)S->g.M * 4;
+    if (z && cudaMemcpyAsync(z, S->z, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (m && cudaMemcpyAsync(m, S->m, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (v && cudaMemcpyAsync(v, S->v, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (t) *t = S->t;
+    return GPAIR_OK;
+}
+
+gpair_status gpair_solver_set_state(gpair_solver* S, const float* z, const float* m, const float* v, int t,
+                                    void* stream) {
+    if (!S || t < 0) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)S->g.M * 4;
+    if (z && cudaMemcpyAsync(S->z, z, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (m && cudaMemcpyAsync(S->m, m, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (v && cudaMemcpyAsync(S->v, v, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    S->t = t;
+    return GPAIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// gpair_internal.cuh -- device-side types and helpers shared by the library's kernels.
+//
+// Geometry precision (Methods, Eq. single_forward): the phase d = R - v t_n of a pair cancels
+// two numbers of ~10 cm to resolve ~10 nm, which FP32 alone cannot do.  Every tile of Gaussians
+// therefore carries a reference point c0; for each (tile, sensor) the distance R0 = |c0 - s| and
+// the phase phi0 = R0 - v t_{n0} at the nearest sample n0 are formed in FP64 once, and each
+// Gaussian adds its small offset delta = c - c0 in FP32 through the cancellation-free form
+//     R - R0 = (2 (c0 - s) . delta + |delta|^2) / (R + R0).
+// The remaining per-sample phase d_m = phi0 + (R - R0) - m * (v / fs) is a sum of small FP32
+// terms, accurate to ~1e-10 m.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gpair.h"
+
+namespace gp {
+
+// Tile of Gaussians processed together.  Grid mode: a BX x BY x BZ brick of lattice nodes
+// (loaded by one 3-D TMA copy); SoA mode: TILE consecutive Gaussians.
+constexpr int TILE = 256;
+constexpr int BX = 8, BY = 8, BZ = 4;
+static_assert(BX * BY * BZ == TILE, "brick must hold one tile");
+
+// Device status word values (set by kernels, read by gpair_last_device_status).
+constexpr int DEV_OK = 0;
+constexpr int DEV_TIMEOUT = 1;
+constexpr int DEV_CAPACITY = 2;
+
+// Bounded wait: iterations of mbarrier.try_wait before a kernel gives up and flags TIMEOUT.
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+struct GaussDev {
+    int grid;                // 1: grid-implicit centres and shared sigma
+    int64_t M;
+    const float *cx, *cy, *cz, *sg, *A;
+    int nx, ny, nz;          // grid mode
+    float h, sigma;
+    double ox, oy, oz;
+    int ntx, nty, ntz;       // bricks per axis (grid mode)
+    int64_t ntiles;
+};
+
+struct ArrDev {
+    int Nd;
+    const float* xyz;
+    float v, fs, t0;
+    int Nt;
+    float k;
+    float Delta;             // v / fs: metres per sample
+    float invDelta;          // fs / v
+};
+
+// Per-tile summary: reference point (float, so that FP64 differences with it are exact), the
+// radius of the tile about it, the widest sigma and the number of valid Gaussians.
+struct TileInfo {
+    float c0x, c0y, c0z;
+    float rad;
+    float smax;
+    int count;
+    int pad0, pad1;
+};
+
+// A slab is the set of tiles one forward CTA walks.  Grid mode: a block of bdx x bdy x bdz
+// bricks starting at brick (bx0, by0, bz0) (compact, so its band of samples is short).  SoA mode:
+// the contiguous tile range [t_begin, t_end).  lo/hi bound the Gaussian centres; smax is the
+// widest sigma.
+struct SlabInfo {
+    float lo[3], hi[3];
+    float smax;
+    int t_begin, t_end;
+    int bx0, by0, bz0;
+    int bdx, bdy, bdz;
+    int pad;
+};
+
+// Per-(tile, sensor) reference, formed in FP64 and rounded once.
+struct PairRef {
+    float v0x, v0y, v0z;     // c0 - s
+    float R0;                // |c0 - s|
+    float phi0;              // R0 - v t_{n0}
+    int n0;                  // nearest sample to the time of flight of c0
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Largest |n0| kept; the host limits n_samples to 2^27, so every window-bound expression of the
+// kernels (w - n0, Nt - 1 - n0, ...) stays inside int32.
+constexpr double N0_CLAMP = 268435456.0;   // 2^28
+
+// Reference for tile centre c0 and sensor s, in FP64.  t_n = t0 + n / fs exactly as the operator
+// defines it.
+__device__ __forceinline__ PairRef make_ref(double c0x, double c0y, double c0z, float sx, float sy,
+                                            float sz, const ArrDev& a) {
+    double vx = c0x - (double)sx, vy = c0y - (double)sy, vz = c0z - (double)sz;
+    double R0 = sqrt(vx * vx + vy * vy + vz * vz);
+    double v = a.v, fs = a.fs, t0 = a.t0;
+    double n0 = rint((R0 / v - t0) * fs);
+    n0 = fmin(fmax(n0, -N0_CLAMP), N0_CLAMP);
+    double phi = R0 - v * (t0 + n0 / fs);
+    PairRef r;
+    r.v0x = (float)vx; r.v0y = (float)vy; r.v0z = (float)vz;
+    r.R0 = (float)R0;
+    r.phi0 = (float)phi;
+    r.n0 = (int)n0;
+    return r;
+}
+
+// Radius of a grid brick about its centre (with a little slack for rounding).
+__host__ __device__ __forceinline__ float brick_radius(float h) {
+    const float hx = 0.5f * (BX - 1), hy = 0.5f * (BY - 1), hz = 0.5f * (BZ - 1);
+    return sqrtf(hx * hx + hy * hy + hz * hz) * h * 1.0001f + 1e-9f;
+}
+
+// Offset of Gaussian l of a grid brick from the brick's reference point (the brick centre).
+__device__ __forceinline__ void brick_offset(int l, float h, float& dx, float& dy, float& dz) {
+    int lx = l & (BX - 1), ly = (l / BX) & (BY - 1), lz = l / (BX * BY);
+    dx = ((float)lx - 0.5f * (BX - 1)) * h;
+    dy = ((float)ly - 0.5f * (BY - 1)) * h;
+    dz = ((float)lz - 0.5f * (BZ - 1)) * h;
+}
+
+// Phase of a pair at the reference sample n0 (d at m = 0) and R, from the reference and the
+// Gaussian's offset (see the header comment).
+__device__ __forceinline__ void pair_phase(const PairRef& r, float dx, float dy, float dz,
+                                           float& R, float& phi) {
+    float num = dx * (2.f * r.v0x + dx) + dy * (2.f * r.v0y + dy) + dz * (2.f * r.v0z + dz);
+    R = sqrtf(fmaf(r.R0, r.R0, num));
+    float dR = num / (r.R0 + R);
+    phi = r.phi0 + dR;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicMax(status, code);
+}
+
+// ---- mbarrier / TMA helpers (sm_90+ PTX; used single-CTA, no multicast) -------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Returns true when the phase with the given parity has completed, false after WAIT_LIMIT
+// unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace gp

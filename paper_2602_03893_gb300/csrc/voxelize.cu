@@ -1,0 +1,113 @@
+// voxelize.cu -- Eq. (2) (the Gaussian source field p0) sampled at voxel centres, each
+// Gaussian truncated to the box |r_a - c_a| <= k sigma on every axis.
+//
+// Lattice case (Gaussians on the output lattice, shared sigma): the field is A convolved with
+// the 1-D taps exp(-(m h)^2 / 2 sigma^2), |m h| <= k sigma, along x, y and z in turn -- three
+// separable gather passes, each one coalesced read and write of the volume (HBM-bound).
+// Any other Gaussian set: each Gaussian scatters its separable box of factors into the volume.
+#include "gpair_internal.cuh"
+
+namespace gp {
+
+constexpr int VOX_MAXTAP = 64;
+
+struct Taps {
+    int mm;                      // taps m = -mm..mm
+    float t[2 * VOX_MAXTAP + 1];
+};
+
+// out = in convolved with taps along one axis (stride s, length n along that axis).
+__global__ void vox_pass_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
+                                int axis, Taps taps) {
+    const int64_t total = (int64_t)nx * ny * nz;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((int64_t)nx * ny));
+        int c, n;
+        int64_t stride;
+        if (axis == 0) { c = ix; n = nx; stride = 1; }
+        else if (axis == 1) { c = iy; n = ny; stride = nx; }
+        else { c = iz; n = nz; stride = (int64_t)nx * ny; }
+        const int lo = max(-taps.mm, -c), hi = min(taps.mm, n - 1 - c);
+        float acc = 0.f;
+        for (int m = lo; m <= hi; ++m) acc = fmaf(taps.t[m + taps.mm], in[v + m * stride], acc);
+        out[v] = acc;
+    }
+}
+
+__global__ void zero_kernel(float* p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0.f;
+}
+
+// One thread per Gaussian: scatter A prod_a f_a into the box of voxels within k sigma per axis.
+__global__ void vox_scatter_kernel(GaussDev g, gpair_grid og, float k, float* __restrict__ vol) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.M) return;
+    const float A = g.A[i];
+    if (A == 0.f) return;
+    float cx, cy, cz, s;
+    if (g.grid) {
+        const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((int64_t)g.nx * g.ny));
+        cx = (float)(g.ox + (ix + 0.5) * (double)g.h);
+        cy = (float)(g.oy + (iy + 0.5) * (double)g.h);
+        cz = (float)(g.oz + (iz + 0.5) * (double)g.h);
+        s = g.sigma;
+    } else {
+        cx = g.cx[i]; cy = g.cy[i]; cz = g.cz[i]; s = g.sg[i];
+    }
+    const float half = k * s * (1.f + 1e-6f), c2 = -0.72134752044448170368f / (s * s);
+    const float inv = 1.f / og.dx;
+    const int xa = max(0, (int)floorf((cx - half - og.ox) * inv - 0.5f)), xb = min(og.nx - 1, (int)ceilf((cx + half - og.ox) * inv - 0.5f));
+    const int ya = max(0, (int)floorf((cy - half - og.oy) * inv - 0.5f)), yb = min(og.ny - 1, (int)ceilf((cy + half - og.oy) * inv - 0.5f));
+    const int za = max(0, (int)floorf((cz - half - og.oz) * inv - 0.5f)), zb = min(og.nz - 1, (int)ceilf((cz + half - og.oz) * inv - 0.5f));
+    for (int iz = za; iz <= zb; ++iz) {
+        const float rz = og.oz + (iz + 0.5f) * og.dx - cz;
+        if (fabsf(rz) > half) continue;
+        const float fz = A * ex2_approx(rz * rz * c2);
+        for (int iy = ya; iy <= yb; ++iy) {
+            const float ry = og.oy + (iy + 0.5f) * og.dx - cy;
+            if (fabsf(ry) > half) continue;
+            const float fyz = fz * ex2_approx(ry * ry * c2);
+            for (int ix = xa; ix <= xb; ++ix) {
+                const float rx = og.ox + (ix + 0.5f) * og.dx - cx;
+                if (fabsf(rx) > half) continue;
+                atomicAdd(&vol[((int64_t)iz * og.ny + iy) * og.nx + ix], fyz * ex2_approx(rx * rx * c2));
+            }
+        }
+    }
+}
+
+static int vox_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+bool vox_is_lattice(const GaussDev& g, const gpair_grid& og) {
+    return g.grid && og.nx == g.nx && og.ny == g.ny && og.nz == g.nz && og.dx == g.h &&
+           (double)og.ox == g.ox && (double)og.oy == g.oy && (double)og.oz == g.oz;
+}
+
+// tmp: scratch volume of the same size (lattice case).
+cudaError_t launch_voxelize(const GaussDev& g, const gpair_grid& og, float k, float* vol, float* tmp, cudaStream_t st) {
+    const int64_t nv = (int64_t)og.nx * og.ny * og.nz;
+    if (vox_is_lattice(g, og)) {
+        Taps taps;
+        const double half = (double)k * g.sigma;
+        int mm = (int)floor(half / g.h * (1.0 + 1e-9));
+        if (mm > VOX_MAXTAP) return cudaErrorInvalidValue;
+        taps.mm = mm;
+        for (int m = -mm; m <= mm; ++m) {
+            double r = m * (double)g.h;
+            taps.t[m + mm] = (float)exp(-r * r / (2.0 * (double)g.sigma * g.sigma));
+        }
+        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(g.A, vol, og.nx, og.ny, og.nz, 0, taps);
+        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, 1, taps);
+        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, 2, taps);
+        return cudaGetLastError();
+    }
+    zero_kernel<<<vox_blocks(nv), 256, 0, st>>>(vol, nv);
+    vox_scatter_kernel<<<(unsigned)((g.M + 255) / 256), 256, 0, st>>>(g, og, k, vol);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

