@@ -109,8 +109,8 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
         if (valid) {
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
-                float R, phi;
-                pair_phase(r, dx, dy, dz, R, phi);
+                float invR, phi;
+                pair_phase_fast(r, dx, dy, dz, invR, phi);
                 const int m_lo = max((int)ceilf((phi - ks) * invDelta), -r.n0);
                 const int m_hi = min((int)floorf((phi + ks) * invDelta), a.Nt - 1 - r.n0);
                 const int off = r.n0 - nbs[q];
@@ -119,11 +119,10 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
                     window_sums<FULL>(bands + q * LBA + off, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
                 else
                     window_sums<FULL>(delta + (size_t)(j0 + q) * a.Nt + r.n0, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
-                const float inv2R = 0.5f / R;
+                const float inv2R = 0.5f * invR;
                 kA.add(s1 * inv2R);
                 if (FULL) {
                     const float wA = Ai * inv2R;
-                    const float invR = 1.f / R;
                     const float gR = wA * (s0 - s2 / (sig * sig)) - wA * s1 * invR;
                     kX.add(gR * (r.v0x + dx) * invR);
                     kY.add(gR * (r.v0y + dy) * invR);

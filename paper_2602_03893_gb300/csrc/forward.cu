@@ -396,6 +396,303 @@ aborted:
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Grid-mode forward with per-(tile, sensor) binning.
+//
+// For one brick and one sensor every pair's window starts at some sample of the tile band.
+// The warp sorts the brick's 256 pairs by that start -- a counting sort whose ranks come from
+// __match_any_sync -- and then walks the bins: lanes take window positions m (G lanes per bin,
+// 32/G bins at a time) and loop over the bin's Gaussians, accumulating sample start + m in a
+// register.  Each (bin, position) sum is added into the warp's tile band once, by plain
+// read-modify-writes ordered group by group (no atomics, deterministic order), and every tile
+// band is added into the slab band with Kahan compensation.
+
+struct FwdGridSmem {
+    float tileA[2][TILE];
+    uint64_t mbar[2];
+    int npass;
+    int abort;
+};
+constexpr size_t FWDG_HDR = (sizeof(FwdGridSmem) + 127) & ~(size_t)127;
+constexpr int FWDG_NCH = 4;      // window chunks of G positions per lane (L <= 4 G)
+
+// Per-warp shared memory of the binned kernel: sorted records (d0, w) | bin offsets [TB + 2] |
+// float tile band [TB] | Kahan slab band (hi, lo) [LB].
+__host__ __device__ __forceinline__ size_t fwdg_warp_bytes(int TB, int LB) {
+    return (size_t)TILE * 8 + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15) + (((size_t)TB * 4 + 15) & ~(size_t)15) +
+           (size_t)LB * 8;
+}
+
+template <int G>
+__global__ void __launch_bounds__(FWD_THREADS, 3)
+fwd_grid_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
+                int2* __restrict__ rows, int LB, int TB, int* status, int use_tma,
+                const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FwdGridSmem& S = *reinterpret_cast<FwdGridSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wbase = smem_raw + FWDG_HDR + (size_t)warp * fwdg_warp_bytes(TB, LB);
+    float2* rec = reinterpret_cast<float2*>(wbase);
+    int* off = reinterpret_cast<int*>(wbase + (size_t)TILE * 8);
+    float* tband = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(off) + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15));
+    float2* lband = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(tband) + (((size_t)TB * 4 + 15) & ~(size_t)15));
+
+    const int slab = blockIdx.y;
+    const int j = blockIdx.x * FWD_SPC + warp;
+    const bool has_sensor = j < a.Nd;
+    const SlabInfo sl = slabs[slab];
+    const int nTiles = sl.t_end - sl.t_begin;
+    const size_t row = (size_t)slab * a.Nd + (has_sensor ? j : 0);
+    float* prow = partial + row * LB;
+
+    // band of samples this (slab, sensor) can touch; one pass by construction of LB
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int n_lo = 0, n_hi = -1;
+    if (has_sensor) {
+        sx = a.xyz[3 * j]; sy = a.xyz[3 * j + 1]; sz = a.xyz[3 * j + 2];
+        if (nTiles > 0) {
+            double dmin, dmax;
+            box_distance(sl, sx, sy, sz, dmin, dmax);
+            double ks = (double)a.k * sl.smax;
+            double lo = floor(((dmin - ks) / a.v - a.t0) * a.fs) - 2.0;
+            double hi = ceil(((dmax + ks) / a.v - a.t0) * a.fs) + 2.0;
+            if (lo < 0) lo = 0;
+            if (hi > a.Nt - 1) hi = a.Nt - 1;
+            if (lo <= hi) { n_lo = (int)lo; n_hi = (int)hi; }
+        }
+    }
+    const int w = n_lo & ~3;
+    bool active = has_sensor && n_lo <= n_hi;
+    if (active && n_hi + 1 - w > LB) {     // cannot happen with the host's band bound
+        set_status(status, DEV_CAPACITY);
+        n_hi = w + LB - 1;
+    }
+    if (lane == 0 && has_sensor) rows[row] = make_int2(w, active ? min(LB, a.Nt - w) : 0);
+    if (threadIdx.x == 0) { S.abort = 0; }
+    const bool tma = use_tma != 0;
+    if (tma && threadIdx.x == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        fence_mbar_init();
+    }
+    for (int q = lane; q < LB; q += 32) lband[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    auto issue = [&](int T) {
+        int tx, ty, tz;
+        slab_brick(sl, T, tx, ty, tz);
+        const int b = T & 1;
+        mbar_arrive_expect_tx(&S.mbar[b], TILE * sizeof(float));
+        tma_load_3d(&S.tileA[b][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.mbar[b]);
+    };
+    if (tma && threadIdx.x == 0) {
+        if (nTiles > 0) issue(0);
+        if (nTiles > 1) issue(1);
+    }
+
+    const float Delta = a.Delta, invDelta = a.invDelta;
+    const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);   // -log2(e) / (2 sigma^2)
+    const float ks = a.k * g.sigma;
+    const float reach = brick_radius(g.h) + ks;
+    const int grp = lane / G, mpos = lane % G;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    PairRef refs;
+    int t = 0;
+    for (; t < nTiles; ++t) {
+        const int b = t & 1;
+        if (tma) {
+            bool ok = mbar_wait(&S.mbar[b], (uint32_t)((t >> 1) & 1));
+            if (!ok) S.abort = 1;
+            __syncthreads();
+            if (S.abort) break;
+        } else {
+            int tx, ty, tz;
+            slab_brick(sl, t, tx, ty, tz);
+            for (int q = threadIdx.x; q < TILE; q += FWD_THREADS) {
+                const int gx = tx * BX + (q & (BX - 1)), gy = ty * BY + ((q / BX) & (BY - 1)), gz = tz * BZ + q / (BX * BY);
+                const bool ok = gx < g.nx && gy < g.ny && gz < g.nz;
+                S.tileA[b][q] = ok ? g.A[((int64_t)gz * g.ny + gy) * g.nx + gx] : 0.f;
+            }
+            __syncthreads();
+        }
+        if (active) {
+            if ((t & 31) == 0 && t + lane < nTiles) {
+                int tx, ty, tz;
+                slab_brick(sl, t + lane, tx, ty, tz);
+                refs = make_ref(g.ox + (tx * BX + BX / 2) * (double)g.h, g.oy + (ty * BY + BY / 2) * (double)g.h,
+                                g.oz + (tz * BZ + BZ / 2) * (double)g.h, sx, sy, sz, a);
+            }
+            const int src = t & 31;
+            PairRef r;
+            r.v0x = __shfl_sync(0xffffffffu, refs.v0x, src);
+            r.v0y = __shfl_sync(0xffffffffu, refs.v0y, src);
+            r.v0z = __shfl_sync(0xffffffffu, refs.v0z, src);
+            r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
+            r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
+            r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
+            int ta = r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2;
+            int tb = r.n0 + (int)ceilf((r.phi0 + reach) * invDelta) + 2;
+            ta = max(ta, w);
+            tb = min(tb, n_hi);
+            if (ta <= tb) {
+                int NB = tb - ta + 1;
+                if (NB > TB) {             // cannot happen with the host's bound on TB
+                    if (lane == 0) set_status(status, DEV_CAPACITY);
+                    NB = TB;
+                    tb = ta + TB - 1;
+                }
+                for (int q = lane; q <= NB; q += 32) off[q] = 0;
+                __syncwarp();
+                // ---- pass 1: one lane per Gaussian; window start (key), rank within the key
+                int key[TILE / 32], rnk[TILE / 32];
+                float d0v[TILE / 32], wv[TILE / 32];
+                int Lmax = 0;
+#pragma unroll
+                for (int q = 0; q < TILE / 32; ++q) {
+                    const int l = lane + 32 * q;
+                    const float Ai = S.tileA[b][l];
+                    float dx, dy, dz, invR, phi;
+                    brick_offset(l, g.h, dx, dy, dz);
+                    pair_phase_fast(r, dx, dy, dz, invR, phi);
+                    const int m_lo = max((int)ceilf((phi - ks) * invDelta), ta - r.n0);
+                    const int m_hi = min((int)floorf((phi + ks) * invDelta), tb - r.n0);
+                    const bool valid = Ai != 0.f && m_lo <= m_hi;
+                    key[q] = valid ? r.n0 + m_lo - ta : NB;
+                    d0v[q] = fmaf(-(float)m_lo, Delta, phi);
+                    wv[q] = Ai * 0.5f * invR;
+                    if (valid) Lmax = max(Lmax, m_hi - m_lo + 1);
+                    const unsigned grpmask = __match_any_sync(0xffffffffu, key[q]);
+                    const int before = __popc(grpmask & lt_mask);
+                    const int base = off[key[q]];
+                    __syncwarp();
+                    if (before == 0) off[key[q]] = base + __popc(grpmask);
+                    __syncwarp();
+                    rnk[q] = base + before;
+                }
+                // ---- exclusive scan of the bin counts (each lane owns a run of bins)
+                {
+                    const int per = (NB + 31) / 32;
+                    const int b0 = lane * per;
+                    int run = 0;
+                    for (int q = 0; q < per; ++q)
+                        if (b0 + q < NB) run += off[b0 + q];
+                    int incl = run;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    int acc = incl - run;
+                    __syncwarp();
+                    for (int q = 0; q < per; ++q)
+                        if (b0 + q < NB) {
+                            const int c = off[b0 + q];
+                            off[b0 + q] = acc;
+                            acc += c;
+                        }
+                    if (lane == 31) off[NB] = incl;
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int q = 0; q < TILE / 32; ++q)
+                    if (key[q] < NB) rec[off[key[q]] + rnk[q]] = make_float2(d0v[q], wv[q]);
+                for (int o = 16; o > 0; o >>= 1) Lmax = max(Lmax, __shfl_xor_sync(0xffffffffu, Lmax, o));
+                int nch = (Lmax + G - 1) / G;
+                if (nch > FWDG_NCH) {      // cannot happen: the host picks the direct kernel then
+                    if (lane == 0) set_status(status, DEV_CAPACITY);
+                    nch = FWDG_NCH;
+                }
+                for (int q = lane; q < NB; q += 32) tband[q] = 0.f;
+                __syncwarp();
+                // ---- pass 2: lanes = window positions, loop over each bin's Gaussians
+                float mD[FWDG_NCH];
+#pragma unroll
+                for (int c = 0; c < FWDG_NCH; ++c) mD[c] = (float)(mpos + c * G) * Delta;
+                for (int b0 = 0; b0 < NB; b0 += 32 / G) {
+                    const int bb = b0 + grp;
+                    const bool bv = bb < NB;
+                    const int start = bv ? off[bb] : 0;
+                    const int cnt = bv ? off[bb + 1] - start : 0;
+                    int niter = cnt;
+                    for (int o = G; o < 32; o <<= 1) niter = max(niter, __shfl_xor_sync(0xffffffffu, niter, o));
+                    if (niter == 0) continue;    // empty bins add nothing (warp-uniform)
+                    float acc[FWDG_NCH];
+#pragma unroll
+                    for (int c = 0; c < FWDG_NCH; ++c) acc[c] = 0.f;
+                    if (nch == 1) {        // every window fits one chunk (the usual case)
+                        const float mD0 = mD[0];
+                        const float2* rp = rec + start;
+                        for (int i = 0; i < niter; ++i) {
+                            // groups with fewer records read a zero record (finite, weight 0)
+                            const float2 rr = (i < cnt) ? rp[i] : make_float2(0.f, 0.f);
+                            const float d = rr.x - mD0;
+                            const float e = ex2_approx(d * d * c2);
+                            const float v = (d >= -ks) ? rr.y * d : 0.f;
+                            acc[0] = fmaf(v, e, acc[0]);
+                        }
+                    } else {
+                        for (int i = 0; i < niter; ++i) {
+                            if (i < cnt) {
+                                const float2 rr = rec[start + i];
+#pragma unroll
+                                for (int c = 0; c < FWDG_NCH; ++c) {
+                                    if (c < nch) {
+                                        const float d = rr.x - mD[c];
+                                        if (d >= -ks) {
+                                            const float e = ex2_approx(d * d * c2);
+                                            acc[c] = fmaf(rr.y * d, e, acc[c]);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    // groups write overlapping samples: one group at a time
+#pragma unroll
+                    for (int gg = 0; gg < 32 / G; ++gg) {
+                        if (grp == gg && bv) {
+#pragma unroll
+                            for (int c = 0; c < FWDG_NCH; ++c) {
+                                const int p = bb + mpos + c * G;
+                                if (c < nch && p < NB) tband[p] += acc[c];
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                // ---- tile band -> slab band (Kahan)
+                for (int q = lane; q < NB; q += 32) {
+                    float2 s = lband[ta - w + q];
+                    const float y = tband[q] - s.y;
+                    const float tt = s.x + y;
+                    s.y = (tt - s.x) - y;
+                    s.x = tt;
+                    lband[ta - w + q] = s;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();   // every warp is done with buffer b
+        if (tma && threadIdx.x == 0 && t + 2 < nTiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + 2);
+        }
+    }
+    if (t < nTiles) {      // a bounded wait ran out
+        set_status(status, DEV_TIMEOUT);
+        if (tma && threadIdx.x == 0)
+            for (int U = t; U < nTiles && U < t + 2; ++U) mbar_wait(&S.mbar[U & 1], (uint32_t)((U >> 1) & 1));
+        return;
+    }
+    if (active) {
+        const int wend = min(a.Nt, w + LB);
+        for (int q = lane; q < wend - w; q += 32) {
+            const float2 s = lband[q];
+            prow[q] = s.x + s.y;
+        }
+    }
+}
+
 // y[j][n] = sum over slabs of the partial rows, fixed slab order.  Banded rows cover
 // [rows.x, rows.x + rows.y); full rows (banded = 0) cover the whole record.
 __global__ void slab_reduce_kernel(const float* __restrict__ partial, const int2* __restrict__ rows, int S, int Nd,
@@ -453,12 +750,28 @@ cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t til
 }
 
 cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
-                           float* partial, int2* rows, int PL, int LB, int TB, int* status,
+                           float* partial, int2* rows, int PL, int LB, int TB, bool binned, int* status,
                            const CUtensorMap* tmap, cudaStream_t st) {
     const size_t smem = fwd_smem_bytes(LB, TB);
     const int banded = g.grid ? 1 : 0;
     dim3 grid((a.Nd + FWD_SPC - 1) / FWD_SPC, S);
     cudaError_t e;
+    const int Lmain = (int)floor(2.0 * a.k * g.sigma * a.invDelta) + 1;   // longest window, samples
+    if (g.grid && binned) {
+        const size_t gsm = FWDG_HDR + (size_t)FWD_SPC * fwdg_warp_bytes(TB, LB);
+        const int use_tma = tmap != nullptr;
+        const CUtensorMap& tm = *(tmap ? tmap : &null_tmap());
+        if (Lmain <= 16) {
+            e = cudaFuncSetAttribute(fwd_grid_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+            if (e != cudaSuccess) return e;
+            fwd_grid_kernel<16><<<grid, FWD_THREADS, gsm, st>>>(g, a, si, partial, rows, LB, TB, status, use_tma, tm);
+        } else {
+            e = cudaFuncSetAttribute(fwd_grid_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+            if (e != cudaSuccess) return e;
+            fwd_grid_kernel<32><<<grid, FWD_THREADS, gsm, st>>>(g, a, si, partial, rows, LB, TB, status, use_tma, tm);
+        }
+        return cudaGetLastError();
+    }
     if (g.grid) {
         e = cudaFuncSetAttribute(fwd_slab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -17,7 +17,7 @@ cudaError_t launch_slab_info_grid(const GaussDev& g, int sbx, int sby, int sbz, 
 cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
                                  cudaStream_t st);
 cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
-                           float* partial, int2* rows, int PL, int LB, int TB, int* status,
+                           float* partial, int2* rows, int PL, int LB, int TB, bool binned, int* status,
                            const CUtensorMap* tmap, cudaStream_t st);
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
@@ -180,6 +180,7 @@ struct FwdPlan {
     int LB;                // slab band entries per sensor (FP64 in shared memory)
     int TB;                // tile band entries per sensor (float, atomics)
     int PL;                // partial row length
+    bool binned;           // grid mode: per-(tile, sensor) binned kernel
     size_t off_ti, off_si, off_rows, off_part, bytes;
 };
 
@@ -215,6 +216,9 @@ FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
         p.PL = p.LB;
         const double reach = brick_radius(g.h) + a.k * g.sigma;
         p.TB = ((int)std::ceil(2.0 * reach * a.invDelta) + 8 + 31) & ~31;
+        // binned kernel: every tile band must fit in TB bins and windows in 4 chunks of 32 lanes
+        const int Lmain = (int)std::floor(2.0 * a.k * g.sigma * a.invDelta) + 1;
+        p.binned = p.TB <= 512 && Lmain <= 128;
         if (p.TB > 512) p.TB = 512;
     } else {
         int64_t S = target_S;
@@ -256,7 +260,8 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
     if (e == cudaSuccess)
-        e = launch_forward(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.TB, status, tma ? &map : nullptr, st);
+        e = launch_forward(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.TB, p.binned, status, tma ? &map : nullptr,
+                           st);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = launch_slab_reduce(g, a, part, rows, p.S, p.PL, y, st);
     return cuda_status(e);
