@@ -49,7 +49,8 @@ typedef enum {
     GPAIR_ERR_NOMEM = 3,         /* scratch/workspace allocation failed */
     GPAIR_ERR_TIMEOUT = 4,       /* a device-side bounded wait ran out (reported on the stream) */
     GPAIR_ERR_UNSUPPORTED = 5,   /* shape outside the supported envelope (e.g. window too long) */
-    GPAIR_ERR_NONFINITE = 6      /* non-finite input detected (validation builds) */
+    GPAIR_ERR_NONFINITE = 6,     /* non-finite input detected (validation builds) */
+    GPAIR_ERR_TOO_LARGE = 7      /* gpair_forward_noalloc: the problem does not fit its fixed scratch */
 } gpair_status;
 
 /* Regular grid of Gaussian centres (Methods, GKD: one Gaussian per voxel centre).
@@ -94,6 +95,25 @@ typedef struct {
  * Accuracy: FP32 arithmetic with the phase R - v t_n referenced to an FP64 per-(tile, sensor)
  * origin; relative L2 error against the FP64 definition ~1e-6 (tested to 1e-5). */
 gpair_status gpair_forward(const gpair_gaussians* g, const gpair_array* arr, float* y, void* stream);
+
+/* ----------------------------------------------------------------------------------------
+ * gpair_forward_noalloc -- gpair_forward for callers that cannot allocate device memory while
+ * they run.  The paper has no counterpart; this is an interface convenience.
+ * Some callers own all device memory through their own arena (a host framework that embeds the
+ * reconstruction) or reserve their memory up front and must not stall or fail on a driver
+ * allocation mid-run (a real-time acquisition loop).  gpair_forward grows a per-stream scratch
+ * pool with cudaMalloc; this entry point instead uses one fixed 64 MiB device array that the
+ * library declares at file scope, so it calls no cudaMalloc, cudaFree or allocating routine.
+ * Every device that loads the library holds those 64 MiB until the process exits.
+ * Same arguments, result and accuracy as gpair_forward (the slab partition may be coarser so
+ * that the scratch fits).  Returns GPAIR_ERR_TOO_LARGE, launching nothing, when the problem
+ * does not fit the array (the 256^3-class grid with 1024 sensors x 4096 samples fits).
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before capturing any stream.  All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (different streams, or several host
+ * threads) race and corrupt each other -- serialise them.  If a device-side bounded wait runs
+ * out, y is filled with NaN. */
+gpair_status gpair_forward_noalloc(const gpair_gaussians* g, const gpair_array* arr, float* y, void* stream);
 
 /* ----------------------------------------------------------------------------------------
  * gpair_adjoint -- the exact transpose of gpair_forward (Methods, adjoint operator: the

@@ -17,12 +17,13 @@ from . import build as _build
 c_int, c_int64, c_float, c_void_p, c_double = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_double
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
-          4: "device-side wait timed out", 5: "unsupported shape or layout", 6: "non-finite input"}
+          4: "device-side wait timed out", 5: "unsupported shape or layout", 6: "non-finite input",
+          7: "problem exceeds the fixed scratch of the allocation-free entry point"}
 
 RULE_ADAM, RULE_GD_LINESEARCH = 0, 1
 
 # Symbols declared in include/gpair.h (checked by the CPU test suite).
-EXPORTS = ("gpair_forward", "gpair_adjoint", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
+EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
@@ -66,6 +67,7 @@ def load(path: str | None = None):
         lib = ctypes.CDLL(path)
         P = c_void_p
         lib.gpair_forward.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P]
+        lib.gpair_forward_noalloc.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P]
         lib.gpair_adjoint.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P, P, P, P]
         lib.gpair_voxelize.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Grid), c_float, P, P]
         lib.gpair_solver_create.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array),
@@ -193,6 +195,17 @@ def gpair_forward(g: Gaussians, arr: SensorArray, y: torch.Tensor, stream=None) 
     gc_, keep = g._c()
     ac = arr._c()
     _check("gpair_forward", lib.gpair_forward(ctypes.byref(gc_), ctypes.byref(ac), _ptr(y), _stream(stream)))
+    return y
+
+
+def gpair_forward_noalloc(g: Gaussians, arr: SensorArray, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """gpair_forward without any device allocation (fixed 64 MiB library-owned scratch; calls
+    overlapping on the GPU race)."""
+    lib = load()
+    gc_, keep = g._c()
+    ac = arr._c()
+    _check("gpair_forward_noalloc", lib.gpair_forward_noalloc(ctypes.byref(gc_), ctypes.byref(ac), _ptr(y),
+                                                              _stream(stream)))
     return y
 
 

@@ -184,6 +184,47 @@ struct FwdPlan {
     size_t off_ti, off_si, off_rows, off_part, bytes;
 };
 
+void plan_offsets(FwdPlan& p, const GaussDev& g, const ArrDev& a) {
+    p.off_ti = 0;
+    p.off_si = align256(sizeof(TileInfo) * (size_t)g.ntiles);
+    p.off_rows = p.off_si + align256(sizeof(SlabInfo) * (size_t)p.S);
+    p.off_part = p.off_rows + align256(sizeof(int2) * (size_t)p.S * a.Nd);
+    p.bytes = p.off_part + align256((size_t)p.S * a.Nd * p.PL * 4);
+}
+
+// Grid mode: slabs are blocks of sb[0] x sb[1] x sb[2] bricks; the band of a block is bounded by
+// its diagonal plus the window, the band of one brick by its radius plus the window.
+void grid_plan_from_blocks(FwdPlan& p, const GaussDev& g, const ArrDev& a, const int sb[3]) {
+    const int nt[3] = {g.ntx, g.nty, g.ntz};
+    const double ext[3] = {BX * (double)g.h, BY * (double)g.h, BZ * (double)g.h};
+    p.sbx = sb[0]; p.sby = sb[1]; p.sbz = sb[2];
+    int64_t s = 1;
+    for (int q = 0; q < 3; ++q) s *= (nt[q] + sb[q] - 1) / sb[q];
+    p.S = (int)s;
+    const double dx = sb[0] * ext[0], dy = sb[1] * ext[1], dz = sb[2] * ext[2];
+    const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+    p.LB = ((int)std::ceil((diag + 2.0 * a.k * g.sigma) * a.invDelta) + 16 + 3) & ~3;
+    p.PL = p.LB;
+    const double reach = brick_radius(g.h) + a.k * g.sigma;
+    p.TB = ((int)std::ceil(2.0 * reach * a.invDelta) + 8 + 31) & ~31;
+    // binned kernel: every tile band must fit in TB bins and windows in 4 chunks of 32 lanes
+    const int Lmain = (int)std::floor(2.0 * a.k * g.sigma * a.invDelta) + 1;
+    p.binned = p.TB <= 512 && Lmain <= 128;
+    if (p.TB > 512) p.TB = 512;
+    plan_offsets(p, g, a);
+}
+
+// SoA mode: S slabs of consecutive tiles, full-record partial rows.
+void soa_plan_from_slabs(FwdPlan& p, const GaussDev& g, const ArrDev& a, int64_t S) {
+    p.tiles_per_slab = (g.ntiles + S - 1) / S;
+    p.S = (int)((g.ntiles + p.tiles_per_slab - 1) / p.tiles_per_slab);
+    p.LB = std::min(512, ((a.Nt + 4) + 3) & ~3);
+    p.PL = a.Nt;
+    p.TB = 256;
+    p.binned = false;
+    plan_offsets(p, g, a);
+}
+
 FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
     FwdPlan p;
     memset(&p, 0, sizeof(p));
@@ -208,36 +249,42 @@ FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
             if (best < 0) break;
             sb[best] = (sb[best] + 1) / 2;
         }
-        p.sbx = sb[0]; p.sby = sb[1]; p.sbz = sb[2];
-        p.S = (int)count();
-        const double dx = sb[0] * ext[0], dy = sb[1] * ext[1], dz = sb[2] * ext[2];
-        const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
-        p.LB = ((int)std::ceil((diag + 2.0 * a.k * g.sigma) * a.invDelta) + 16 + 3) & ~3;
-        p.PL = p.LB;
-        const double reach = brick_radius(g.h) + a.k * g.sigma;
-        p.TB = ((int)std::ceil(2.0 * reach * a.invDelta) + 8 + 31) & ~31;
-        // binned kernel: every tile band must fit in TB bins and windows in 4 chunks of 32 lanes
-        const int Lmain = (int)std::floor(2.0 * a.k * g.sigma * a.invDelta) + 1;
-        p.binned = p.TB <= 512 && Lmain <= 128;
-        if (p.TB > 512) p.TB = 512;
+        grid_plan_from_blocks(p, g, a, sb);
     } else {
         int64_t S = target_S;
         if (S > g.ntiles) S = g.ntiles;
         const int64_t row = (int64_t)a.Nd * a.Nt * 4;
         while (S > 1 && S * row > ((int64_t)2 << 30)) S = (S + 1) / 2;
         if (S < 1) S = 1;
-        p.tiles_per_slab = (g.ntiles + S - 1) / S;
-        p.S = (int)((g.ntiles + p.tiles_per_slab - 1) / p.tiles_per_slab);
-        p.LB = std::min(512, ((a.Nt + 4) + 3) & ~3);
-        p.PL = a.Nt;
-        p.TB = 256;
+        soa_plan_from_slabs(p, g, a, S);
     }
-    p.off_ti = 0;
-    p.off_si = align256(sizeof(TileInfo) * (size_t)g.ntiles);
-    p.off_rows = p.off_si + align256(sizeof(SlabInfo) * (size_t)p.S);
-    p.off_part = p.off_rows + align256(sizeof(int2) * (size_t)p.S * a.Nd);
-    p.bytes = p.off_part + align256((size_t)p.S * a.Nd * p.PL * 4);
     return p;
+}
+
+// Plan for a fixed scratch capacity (used by the allocation-free entry point): the default plan,
+// coarsened -- larger slab blocks, or fewer slabs -- until its scratch fits in `cap` bytes.
+// Returns false when even the coarsest plan does not fit.
+bool plan_forward_capped(const GaussDev& g, const ArrDev& a, size_t cap, FwdPlan& out) {
+    FwdPlan p = plan_forward(g, a);
+    if (g.grid) {
+        int sb[3] = {p.sbx, p.sby, p.sbz};
+        const int nt[3] = {g.ntx, g.nty, g.ntz};
+        const double ext[3] = {BX * (double)g.h, BY * (double)g.h, BZ * (double)g.h};
+        while (p.bytes > cap) {
+            int best = -1;
+            for (int q = 0; q < 3; ++q)
+                if (sb[q] < nt[q] && (best < 0 || sb[q] * ext[q] < sb[best] * ext[best])) best = q;
+            if (best < 0) return false;
+            sb[best] = std::min(nt[best], 2 * sb[best]);
+            grid_plan_from_blocks(p, g, a, sb);
+        }
+        if (p.LB > 2048) return false;    // slab band beyond the kernel's shared-memory budget
+    } else {
+        while (p.bytes > cap && p.S > 1) soa_plan_from_slabs(p, g, a, (p.S + 1) / 2);
+        if (p.bytes > cap) return false;
+    }
+    out = p;
+    return true;
 }
 
 // ev (optional): two events recorded immediately before and after the slab kernel.
@@ -284,6 +331,24 @@ gpair_status run_adjoint(const GaussDev& g, const ArrDev& a, const float* delta,
 
 }  // namespace
 
+namespace gp {
+// The forward operator run entirely inside caller-provided scratch (`cap` bytes of device memory
+// at `scratch`, plus a device status word): validates, plans within the capacity and launches.
+// Allocates nothing.  Used by the allocation-free entry point.
+gpair_status forward_into_scratch(const gpair_gaussians* gi, const gpair_array* ai, float* y, cudaStream_t st,
+                                  void* scratch, size_t cap, int* status) {
+    GaussDev g;
+    ArrDev a;
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (!y) return GPAIR_ERR_INVALID_ARG;
+    FwdPlan p;
+    if (!plan_forward_capped(g, a, cap, p)) return GPAIR_ERR_TOO_LARGE;
+    return run_forward(g, a, y, st, scratch, status, p);
+}
+}  // namespace gp
+
 // ============================================================================================
 // Public entry points.
 
@@ -300,6 +365,7 @@ const char* gpair_status_string(gpair_status s) {
         case GPAIR_ERR_TIMEOUT: return "device-side wait timed out";
         case GPAIR_ERR_UNSUPPORTED: return "unsupported shape or layout";
         case GPAIR_ERR_NONFINITE: return "non-finite input";
+        case GPAIR_ERR_TOO_LARGE: return "problem needs more scratch than the allocation-free entry point holds";
     }
     return "unknown status";
 }

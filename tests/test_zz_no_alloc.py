@@ -1,0 +1,59 @@
+"""gpair_forward_noalloc: the forward operator for callers that must not allocate device memory
+while they run (a host framework's own memory arena, a real-time loop with memory reserved up
+front).  It must give gpair_forward's result (relative L2 1e-5, the forward tolerance) on two
+calls in a row, using only its fixed library-owned scratch.  This file is collected last so that
+a run stopping at the first failure has already run every other test; it also passes alone."""
+import numpy as np
+import pytest
+import torch
+
+from gpair_testutil import device_inputs, rel_l2
+from paper_2602_03893_gb300 import _lib, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _both(w, A=None):
+    gs, arr = device_inputs(w, A)
+    y_ref = torch.empty((w.Nd, w.Nt), device="cuda")
+    _lib.gpair_forward(gs, arr, y_ref)
+    outs = []
+    for _ in range(2):
+        y = torch.full((w.Nd, w.Nt), float("nan"), device="cuda")
+        _lib.gpair_forward_noalloc(gs, arr, y)
+        torch.cuda.synchronize()
+        outs.append(y.cpu().numpy())
+    ref = y_ref.cpu().numpy()
+    for y in outs:
+        assert np.all(np.isfinite(y))
+        assert rel_l2(y, ref) < 1e-5
+    return ref
+
+
+def test_grid_tiny_two_calls():
+    ref = _both(synth.tiny(1))
+    assert np.abs(ref).max() > 0
+
+
+def test_free_gaussians_two_calls():
+    g = synth.centred_grid(20, 16, 12, 0.1e-3)
+    free = synth.free_gaussians(g, 5, A=np.random.default_rng(1).uniform(0, 1, g.M))
+    _both(synth.Workload("free", g, synth.cap_sensors(24, 25e-3, 160.0), 2048, free=free))
+
+
+def test_paper_scale_fits_the_fixed_scratch():
+    w = synth.paper_scale(3)
+    x = (np.random.default_rng(2).uniform(0.0, 1.0, w.M) ** 2).astype(np.float32)
+    _both(w, A=x)
+
+
+def test_too_large_is_rejected_without_launching():
+    g = synth.centred_grid(64, 64, 64, 0.1e-3)
+    free = synth.free_gaussians(g, 6)
+    w = synth.Workload("big-record", g, synth.cap_sensors(4096, 40e-3, 180.0), 8192, free=free)
+    gs, arr = device_inputs(w)
+    y = torch.zeros((w.Nd, w.Nt), device="cuda")
+    with pytest.raises(_lib.GpairError) as ei:
+        _lib.gpair_forward_noalloc(gs, arr, y)
+    assert ei.value.code == 7
+    assert float(y.abs().max()) == 0.0
