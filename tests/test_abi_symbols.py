@@ -12,10 +12,15 @@ from paper_2602_03893_gb300 import _lib, build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "gpair.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gpair_[a-z0-9_]+)\s*\(", src)))
+def declared_functions(header=None):
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h") or (header and h != header):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+        names |= set(re.findall(r"\b(gpair_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -28,9 +33,9 @@ def test_header_declarations_are_all_exported(lib):
     names = declared_functions()
     assert "gpair_forward" in names and "gpair_adjoint" in names and "gpair_step" in names
     for n in names:
-        assert hasattr(lib, n), f"{n} declared in gpair.h but not exported"
-    assert set(names) == set(_lib.EXPORTS) | {n for n in names if n not in _lib.EXPORTS}
-    assert set(_lib.EXPORTS) <= set(names)
+        assert hasattr(lib, n), f"{n} declared in include/*.h but not exported"
+    assert set(_lib.EXPORTS) == set(declared_functions("gpair.h"))
+    assert "gpair_conv3d_fwd" in names and "gpair_conv3d_wgrad" in names
 
 
 def test_status_strings_and_version(lib):
