@@ -146,6 +146,117 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Amplitude gradient for a grid with shared sigma through the sub-sample expansion
+// (MomentTable): for a pair whose window starts at sample b with offset e,
+//     sum_m delta[b + m] K(d0 - m Delta) = sum_p e^p Q_p[b] (+ the conditional last position),
+//     Q_p[b] = sum_{m < L} delta[b + m] c[m][p],
+// so one table of L-tap correlations per sensor replaces the per-sample evaluation.
+
+// Q[j][b + L][p] for window starts b in [-L, N_t): the residual is zero outside the record.
+__global__ void __launch_bounds__(256)
+adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ MomentTable T, float* __restrict__ Q) {
+    extern __shared__ float sd[];   // residual samples b0 .. b0 + 256 + L
+    const int j = blockIdx.y;
+    const int L = T.L;
+    const int b0 = -L + blockIdx.x * 256;
+    const float* dj = delta + (size_t)j * Nt;
+    for (int q = threadIdx.x; q < 256 + L; q += blockDim.x) {
+        const int n = b0 + q;
+        sd[q] = (n >= 0 && n < Nt) ? dj[n] : 0.f;
+    }
+    __syncthreads();
+    const int b = b0 + (int)threadIdx.x;
+    if (b >= Nt) return;
+    float acc[MOM_P];
+#pragma unroll
+    for (int p = 0; p < MOM_P; ++p) acc[p] = 0.f;
+    for (int m = 0; m < L; ++m) {
+        const float dl = sd[threadIdx.x + m];
+#pragma unroll
+        for (int p = 0; p < MOM_P; ++p) acc[p] = fmaf(dl, T.c[m][p], acc[p]);
+    }
+    float4* dst = reinterpret_cast<float4*>(Q + ((size_t)j * (Nt + L) + (b + L)) * MOM_P);
+    dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+
+// One CTA per brick of 256 grid Gaussians, one thread per Gaussian, all sensors in chunks of 32.
+__global__ void __launch_bounds__(ADJ_THREADS)
+adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const float* __restrict__ Q,
+                  const __grid_constant__ MomentTable T, float* __restrict__ gA) {
+    __shared__ PairRef refs[ADJ_SC];
+    const int64_t t = blockIdx.x;
+    const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
+    const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
+    const int gx = tx * BX + (l & (BX - 1)), gy = ty * BY + ((l / BX) & (BY - 1)), gz = tz * BZ + l / (BX * BY);
+    const bool valid = gx < g.nx && gy < g.ny && gz < g.nz;
+    const int64_t i = ((int64_t)gz * g.ny + gy) * g.nx + gx;
+    float dx, dy, dz;
+    brick_offset(l, g.h, dx, dy, dz);
+    const double c0x = g.ox + (tx * BX + BX / 2) * (double)g.h;
+    const double c0y = g.oy + (ty * BY + BY / 2) * (double)g.h;
+    const double c0z = g.oz + (tz * BZ + BZ / 2) * (double)g.h;
+    const float ks = a.k * g.sigma, Delta = a.Delta, invDelta = a.invDelta;
+    const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
+    const int L = T.L, Nt = a.Nt;
+    const float LD = (float)L * Delta;
+    KahanF kA;
+    for (int j0 = 0; j0 < a.Nd; j0 += ADJ_SC) {
+        const int nsc = min(ADJ_SC, a.Nd - j0);
+        if (warp == 0 && lane < nsc) {
+            const int j = j0 + lane;
+            refs[lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        }
+        __syncthreads();
+        if (valid) {
+            for (int q = 0; q < nsc; ++q) {
+                const PairRef r = refs[q];
+                float invR, phi;
+                pair_phase_fast(r, dx, dy, dz, invR, phi);
+                const int m_lo = (int)ceilf((phi - ks) * invDelta);
+                const int b = r.n0 + m_lo;
+                if (b < -L || b >= Nt) continue;
+                const float d0 = fmaf(-(float)m_lo, Delta, phi);
+                const float e = (d0 - T.dstar) * T.inv_half;
+                const float4* qp = reinterpret_cast<const float4*>(Q + ((size_t)(j0 + q) * (Nt + L) + (b + L)) * MOM_P);
+                const float4 q0 = __ldg(qp), q1 = __ldg(qp + 1);
+                float s = q1.w;
+                s = fmaf(s, e, q1.z);
+                s = fmaf(s, e, q1.y);
+                s = fmaf(s, e, q1.x);
+                s = fmaf(s, e, q0.w);
+                s = fmaf(s, e, q0.z);
+                s = fmaf(s, e, q0.y);
+                s = fmaf(s, e, q0.x);
+                const float dL = d0 - LD;              // window position L, inside only at the edge
+                if (dL >= -ks) {
+                    const int n = b + L;
+                    if (n >= 0 && n < Nt) s = fmaf(delta[(size_t)(j0 + q) * Nt + n] * dL, ex2_approx(dL * dL * c2), s);
+                }
+                kA.add(s * 0.5f * invR);
+            }
+        }
+        __syncthreads();
+    }
+    if (valid) gA[i] = kA.s;
+}
+
+size_t adj_moment_q_bytes(const ArrDev& a, int L) { return (size_t)a.Nd * (a.Nt + L) * MOM_P * sizeof(float); }
+
+cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const float* delta, float* gA,
+                                  const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st) {
+    dim3 qgrid((a.Nt + T.L + 255) / 256, a.Nd);
+    adj_q_kernel<<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    adj_moment_kernel<<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+    return e;
+}
+
 int adj_band_len(float rad, float smax, float k, float invDelta) {
     int half = (int)ceilf((rad + k * smax) * invDelta) + 4;
     int lb = 2 * half + 8;

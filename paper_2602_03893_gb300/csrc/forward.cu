@@ -693,6 +693,249 @@ fwd_grid_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Grid-mode forward through the sub-sample expansion (MomentTable).  Binning as above, but each
+// pair is reduced to its window-start bin b and offset e: the slab keeps, per bin, the moments
+//     Z_p[b] = sum over the slab's pairs starting at b of w e^p     (p < MOM_P)
+// and the signal is their correlation with the table, y[n] = sum_{m<L} sum_p c[m][p] Z_p[n - m],
+// plus the few pairs whose window also holds position L (evaluated directly).  Lanes own bins:
+// a lane sums the moments of its bin's records in registers and adds them into the slab's
+// moment band; no atomics except the rare direct terms.
+
+__host__ __device__ __forceinline__ size_t fwdm_warp_bytes(int TB, int LB, int L) {
+    return (size_t)TILE * 8 + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15) + (size_t)(LB + L) * MOM_P * 4 +
+           (((size_t)LB * 4 + 15) & ~(size_t)15);
+}
+
+__global__ void __launch_bounds__(FWD_THREADS, 2)
+fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
+                  int2* __restrict__ rows, int LB, int TB, int* status, int use_tma,
+                  const __grid_constant__ CUtensorMap tmap, const __grid_constant__ MomentTable T) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FwdGridSmem& S = *reinterpret_cast<FwdGridSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = T.L;
+    unsigned char* wbase = smem_raw + FWDG_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L);
+    float2* rec = reinterpret_cast<float2*>(wbase);
+    int* off = reinterpret_cast<int*>(wbase + (size_t)TILE * 8);
+    float* Z = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(off) + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15));
+    float* xband = Z + (size_t)(LB + L) * MOM_P;
+
+    const int slab = blockIdx.y;
+    const int j = blockIdx.x * FWD_SPC + warp;
+    const bool has_sensor = j < a.Nd;
+    const SlabInfo sl = slabs[slab];
+    const int nTiles = sl.t_end - sl.t_begin;
+    const size_t row = (size_t)slab * a.Nd + (has_sensor ? j : 0);
+    float* prow = partial + row * LB;
+
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int n_lo = 0, n_hi = -1;
+    if (has_sensor) {
+        sx = a.xyz[3 * j]; sy = a.xyz[3 * j + 1]; sz = a.xyz[3 * j + 2];
+        if (nTiles > 0) {
+            double dmin, dmax;
+            box_distance(sl, sx, sy, sz, dmin, dmax);
+            double ks = (double)a.k * sl.smax;
+            double lo = floor(((dmin - ks) / a.v - a.t0) * a.fs) - 2.0;
+            double hi = ceil(((dmax + ks) / a.v - a.t0) * a.fs) + 2.0;
+            if (lo < 0) lo = 0;
+            if (hi > a.Nt - 1) hi = a.Nt - 1;
+            if (lo <= hi) { n_lo = (int)lo; n_hi = (int)hi; }
+        }
+    }
+    const int w = n_lo & ~3;
+    bool active = has_sensor && n_lo <= n_hi;
+    if (active && n_hi + 1 - w > LB) {     // cannot happen with the host's band bound
+        set_status(status, DEV_CAPACITY);
+        n_hi = w + LB - 1;
+    }
+    if (lane == 0 && has_sensor) rows[row] = make_int2(w, active ? min(LB, a.Nt - w) : 0);
+    if (threadIdx.x == 0) S.abort = 0;
+    const bool tma = use_tma != 0;
+    if (tma && threadIdx.x == 0) {
+        mbar_init(&S.mbar[0], 1);
+        mbar_init(&S.mbar[1], 1);
+        fence_mbar_init();
+    }
+    for (int q = lane; q < (LB + L) * MOM_P; q += 32) Z[q] = 0.f;
+    for (int q = lane; q < LB; q += 32) xband[q] = 0.f;
+    __syncthreads();
+
+    auto issue = [&](int TT) {
+        int tx, ty, tz;
+        slab_brick(sl, TT, tx, ty, tz);
+        const int b = TT & 1;
+        mbar_arrive_expect_tx(&S.mbar[b], TILE * sizeof(float));
+        tma_load_3d(&S.tileA[b][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.mbar[b]);
+    };
+    if (tma && threadIdx.x == 0) {
+        if (nTiles > 0) issue(0);
+        if (nTiles > 1) issue(1);
+    }
+
+    const float Delta = a.Delta, invDelta = a.invDelta;
+    const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
+    const float ks = a.k * g.sigma;
+    const float reach = brick_radius(g.h) + ks;
+    const float LD = (float)L * Delta;
+    const int zlo = w - L;                 // first bin of the moment band
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    PairRef refs;
+    int t = 0;
+    for (; t < nTiles; ++t) {
+        const int b = t & 1;
+        if (tma) {
+            bool ok = mbar_wait(&S.mbar[b], (uint32_t)((t >> 1) & 1));
+            if (!ok) S.abort = 1;
+            __syncthreads();
+            if (S.abort) break;
+        } else {
+            int tx, ty, tz;
+            slab_brick(sl, t, tx, ty, tz);
+            for (int q = threadIdx.x; q < TILE; q += FWD_THREADS) {
+                const int gx = tx * BX + (q & (BX - 1)), gy = ty * BY + ((q / BX) & (BY - 1)), gz = tz * BZ + q / (BX * BY);
+                const bool ok = gx < g.nx && gy < g.ny && gz < g.nz;
+                S.tileA[b][q] = ok ? g.A[((int64_t)gz * g.ny + gy) * g.nx + gx] : 0.f;
+            }
+            __syncthreads();
+        }
+        if (active) {
+            if ((t & 31) == 0 && t + lane < nTiles) {
+                int tx, ty, tz;
+                slab_brick(sl, t + lane, tx, ty, tz);
+                refs = make_ref(g.ox + (tx * BX + BX / 2) * (double)g.h, g.oy + (ty * BY + BY / 2) * (double)g.h,
+                                g.oz + (tz * BZ + BZ / 2) * (double)g.h, sx, sy, sz, a);
+            }
+            const int src = t & 31;
+            PairRef r;
+            r.v0x = __shfl_sync(0xffffffffu, refs.v0x, src);
+            r.v0y = __shfl_sync(0xffffffffu, refs.v0y, src);
+            r.v0z = __shfl_sync(0xffffffffu, refs.v0z, src);
+            r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
+            r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
+            r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
+            // window-start bins this tile can produce that reach this slab's samples
+            int ta = r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2;
+            int tb = r.n0 + (int)ceilf((r.phi0 + reach) * invDelta) + 2;
+            ta = max(ta, zlo);
+            tb = min(tb, n_hi);
+            if (ta <= tb) {
+                int NB = tb - ta + 1;
+                if (NB > TB) {
+                    if (lane == 0) set_status(status, DEV_CAPACITY);
+                    NB = TB;
+                    tb = ta + TB - 1;
+                }
+                for (int q = lane; q <= NB; q += 32) off[q] = 0;
+                __syncwarp();
+                int key[TILE / 32], rnk[TILE / 32];
+                float ev[TILE / 32], wv[TILE / 32];
+#pragma unroll
+                for (int q = 0; q < TILE / 32; ++q) {
+                    const int l = lane + 32 * q;
+                    const float Ai = S.tileA[b][l];
+                    float dx, dy, dz, invR, phi;
+                    brick_offset(l, g.h, dx, dy, dz);
+                    pair_phase_fast(r, dx, dy, dz, invR, phi);
+                    const int m_lo = (int)ceilf((phi - ks) * invDelta);
+                    const int bin = r.n0 + m_lo;
+                    const bool valid = Ai != 0.f && bin >= ta && bin <= tb;
+                    key[q] = valid ? bin - ta : NB;
+                    const float d0 = fmaf(-(float)m_lo, Delta, phi);
+                    ev[q] = (d0 - T.dstar) * T.inv_half;
+                    wv[q] = Ai * 0.5f * invR;
+                    // window position L: inside only at the window edge; added directly
+                    const float dL = d0 - LD;
+                    const int nL = bin + L;
+                    if (valid && dL >= -ks && nL >= w && nL <= n_hi)
+                        atomicAdd(&xband[nL - w], wv[q] * dL * ex2_approx(dL * dL * c2));
+                    const unsigned grpmask = __match_any_sync(0xffffffffu, key[q]);
+                    const int before = __popc(grpmask & lt_mask);
+                    const int base = off[key[q]];
+                    __syncwarp();
+                    if (before == 0) off[key[q]] = base + __popc(grpmask);
+                    __syncwarp();
+                    rnk[q] = base + before;
+                }
+                {   // exclusive scan of the bin counts
+                    const int per = (NB + 31) / 32;
+                    const int b0 = lane * per;
+                    int run = 0;
+                    for (int q = 0; q < per; ++q)
+                        if (b0 + q < NB) run += off[b0 + q];
+                    int incl = run;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    int acc = incl - run;
+                    __syncwarp();
+                    for (int q = 0; q < per; ++q)
+                        if (b0 + q < NB) {
+                            const int c = off[b0 + q];
+                            off[b0 + q] = acc;
+                            acc += c;
+                        }
+                    if (lane == 31) off[NB] = incl;
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int q = 0; q < TILE / 32; ++q)
+                    if (key[q] < NB) rec[off[key[q]] + rnk[q]] = make_float2(ev[q], wv[q]);
+                __syncwarp();
+                // lanes own bins: moments in registers, then one add into the moment band
+                for (int bb = lane; bb < NB; bb += 32) {
+                    const int start = off[bb], end = off[bb + 1];
+                    if (start == end) continue;
+                    float M[MOM_P];
+#pragma unroll
+                    for (int p = 0; p < MOM_P; ++p) M[p] = 0.f;
+                    for (int i = start; i < end; ++i) {
+                        const float2 rr = rec[i];
+                        float tt = rr.y;
+#pragma unroll
+                        for (int p = 0; p < MOM_P; ++p) {
+                            M[p] += tt;
+                            tt *= rr.x;
+                        }
+                    }
+                    float* zp = Z + (size_t)(ta + bb - zlo) * MOM_P;
+#pragma unroll
+                    for (int p = 0; p < MOM_P; ++p) zp[p] += M[p];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();   // every warp is done with buffer b
+        if (tma && threadIdx.x == 0 && t + 2 < nTiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + 2);
+        }
+    }
+    if (t < nTiles) {      // a bounded wait ran out
+        set_status(status, DEV_TIMEOUT);
+        if (tma && threadIdx.x == 0)
+            for (int U = t; U < nTiles && U < t + 2; ++U) mbar_wait(&S.mbar[U & 1], (uint32_t)((U >> 1) & 1));
+        return;
+    }
+    if (active) {
+        // y[n] = sum_{m<L} sum_p c[m][p] Z_p[n - m] + direct terms, for the slab's samples
+        const int wend = min(a.Nt, w + LB);
+        for (int q = lane; q < wend - w; q += 32) {
+            float y = xband[q];
+            const float* zb = Z + (size_t)(q + L) * MOM_P;   // bin n = w + q sits at index q + L
+            for (int m = 0; m < L; ++m) {
+                const float* zm = zb - (size_t)m * MOM_P;
+#pragma unroll
+                for (int p = 0; p < MOM_P; ++p) y = fmaf(T.c[m][p], zm[p], y);
+            }
+            prow[q] = y;
+        }
+    }
+}
+
 // y[j][n] = sum over slabs of the partial rows, fixed slab order.  Banded rows cover
 // [rows.x, rows.x + rows.y); full rows (banded = 0) cover the whole record.
 __global__ void slab_reduce_kernel(const float* __restrict__ partial, const int2* __restrict__ rows, int S, int Nd,
@@ -751,11 +994,21 @@ cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t til
 
 cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
                            float* partial, int2* rows, int PL, int LB, int TB, bool binned, int* status,
-                           const CUtensorMap* tmap, cudaStream_t st) {
+                           const CUtensorMap* tmap, const MomentTable* mom, cudaStream_t st) {
     const size_t smem = fwd_smem_bytes(LB, TB);
     const int banded = g.grid ? 1 : 0;
     dim3 grid((a.Nd + FWD_SPC - 1) / FWD_SPC, S);
     cudaError_t e;
+    if (g.grid && binned && mom) {
+        const size_t msm = FWDG_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TB, LB, mom->L);
+        if (msm <= 227 * 1024) {
+            e = cudaFuncSetAttribute(fwd_moment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+            if (e != cudaSuccess) return e;
+            fwd_moment_kernel<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TB, status, tmap != nullptr,
+                                                              *(tmap ? tmap : &null_tmap()), *mom);
+            return cudaGetLastError();
+        }
+    }
     const int Lmain = (int)floor(2.0 * a.k * g.sigma * a.invDelta) + 1;   // longest window, samples
     if (g.grid && binned) {
         const size_t gsm = FWDG_HDR + (size_t)FWD_SPC * fwdg_warp_bytes(TB, LB);

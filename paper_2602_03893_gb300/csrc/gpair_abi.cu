@@ -18,12 +18,15 @@ cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t til
                                  cudaStream_t st);
 cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
                            float* partial, int2* rows, int PL, int LB, int TB, bool binned, int* status,
-                           const CUtensorMap* tmap, cudaStream_t st);
+                           const CUtensorMap* tmap, const MomentTable* mom, cudaStream_t st);
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
 int adj_band_len(float rad, float smax, float k, float invDelta);
 cudaError_t launch_adjoint(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const float* delta, float* gA,
                            float* gc, float* gs, int LBA, cudaStream_t st);
+size_t adj_moment_q_bytes(const ArrDev& a, int L);
+cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const float* delta, float* gA,
+                                  const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
 cudaError_t launch_resid(const float* y, const float* b, float* delta, float scale, int64_t n, double* partial,
                          double* out, cudaStream_t st);
@@ -287,6 +290,8 @@ bool plan_forward_capped(const GaussDev& g, const ArrDev& a, size_t cap, FwdPlan
     return true;
 }
 
+bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T);
+
 // ev (optional): two events recorded immediately before and after the slab kernel.
 gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStream_t st, void* scratch, int* status,
                          const FwdPlan& p, const cudaEvent_t* ev = nullptr) {
@@ -306,12 +311,48 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
         if (e == cudaSuccess) e = launch_slab_info_soa(ti, g.ntiles, p.tiles_per_slab, p.S, si, st);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+    MomentTable mom;
+    const bool use_mom = g.grid && make_moment_table(g, a, mom);
     if (e == cudaSuccess)
         e = launch_forward(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.TB, p.binned, status, tma ? &map : nullptr,
-                           st);
+                           use_mom ? &mom : nullptr, st);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess) e = launch_slab_reduce(g, a, part, rows, p.S, p.PL, y, st);
     return cuda_status(e);
+}
+
+// Coefficients of the sub-sample expansion (MomentTable, gpair_internal.cuh) for a shared sigma.
+// K(d) = d exp(-d^2/2s^2) has derivatives K^(p)(d) = s^(1-p) (-1)^p He_{p+1}(u) exp(-u^2/2),
+// u = d / s, with He the probabilists' Hermite polynomials.  Returns false when the expansion
+// does not apply (window longer than MOM_LMAX samples, or Delta > sigma / 2 where 8 terms no
+// longer reach 1e-6).
+bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
+    if (!g.grid) return false;
+    const double s = g.sigma, Delta = (double)a.Delta, k = a.k;
+    const double X = 2.0 * k * s / Delta;
+    const int L = (int)std::floor(X);
+    if (L < 1 || L > MOM_LMAX || Delta > 0.5 * s) return false;
+    const double dstar = k * s - 0.5 * Delta;
+    T.L = L;
+    T.dstar = (float)dstar;
+    T.inv_half = (float)(2.0 / Delta);
+    for (int m = 0; m < MOM_LMAX; ++m)
+        for (int p = 0; p < MOM_P; ++p) T.c[m][p] = 0.f;
+    for (int m = 0; m < L; ++m) {
+        const double u = (dstar - m * Delta) / s;
+        double He[MOM_P + 2];
+        He[0] = 1.0;
+        He[1] = u;
+        for (int n = 1; n <= MOM_P; ++n) He[n + 1] = u * He[n] - n * He[n - 1];
+        const double eu = std::exp(-0.5 * u * u);
+        double fact = 1.0, hp = 1.0, sp = s;   // p!, (Delta/2)^p, s^(1-p)
+        for (int p = 0; p < MOM_P; ++p) {
+            if (p > 0) { fact *= p; hp *= 0.5 * Delta; sp /= s; }
+            const double deriv = sp * ((p & 1) ? -1.0 : 1.0) * He[p + 1] * eu;
+            T.c[m][p] = (float)(deriv * hp / fact);
+        }
+    }
+    return true;
 }
 
 int adjoint_band(const GaussDev& g, const ArrDev& a) {
@@ -319,8 +360,21 @@ int adjoint_band(const GaussDev& g, const ArrDev& a) {
     return 256;
 }
 
+// Bytes of the expansion table Q an amplitude-only grid adjoint needs (0 when it does not apply).
+size_t adjoint_q_bytes(const GaussDev& g, const ArrDev& a) {
+    MomentTable T;
+    if (!make_moment_table(g, a, T)) return 0;
+    return align256(adj_moment_q_bytes(a, T.L));
+}
+
+// qbuf (optional): adjoint_q_bytes() of device memory for the expansion path.
 gpair_status run_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, float* gc, float* gs,
-                         cudaStream_t st, void* scratch, const cudaEvent_t* ev = nullptr) {
+                         cudaStream_t st, void* scratch, const cudaEvent_t* ev = nullptr, void* qbuf = nullptr) {
+    if (qbuf && !gc && !gs) {
+        MomentTable T;
+        if (make_moment_table(g, a, T))
+            return cuda_status(launch_adjoint_moment(g, a, delta, gA, T, static_cast<float*>(qbuf), ev, st));
+    }
     TileInfo* ti = static_cast<TileInfo*>(scratch);
     cudaError_t e = launch_tile_info(g, ti, st);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
@@ -395,8 +449,11 @@ gpair_status gpair_adjoint(const gpair_gaussians* gi, const gpair_array* ai, con
     if (!delta || !gA) return GPAIR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* scratch = nullptr;
-    if ((s = get_scratch(st, align256(sizeof(TileInfo) * (size_t)g.ntiles), &scratch, nullptr)) != GPAIR_OK) return s;
-    return run_adjoint(g, a, delta, gA, gc, gsigma, st, scratch);
+    const size_t ti_bytes = align256(sizeof(TileInfo) * (size_t)g.ntiles);
+    const size_t q_bytes = (gc || gsigma) ? 0 : adjoint_q_bytes(g, a);
+    if ((s = get_scratch(st, ti_bytes + q_bytes, &scratch, nullptr)) != GPAIR_OK) return s;
+    return run_adjoint(g, a, delta, gA, gc, gsigma, st, scratch, nullptr,
+                       q_bytes ? static_cast<char*>(scratch) + ti_bytes : nullptr);
 }
 
 gpair_status gpair_voxelize(const gpair_gaussians* gi, const gpair_grid* og, float window_k, float* vol,
@@ -468,6 +525,7 @@ struct gpair_solver {
     float *y = nullptr, *delta = nullptr, *Fg = nullptr;
     double* red = nullptr;   // reduction partials (2 * red_blocks) + results (4)
     void* fwd_scratch = nullptr;
+    void* qbuf = nullptr;    // expansion table of the amplitude adjoint (grid Gaussians)
     int* status = nullptr;
     FwdPlan plan;
     // Profiling (gpair_solver_profile): per recorded step six events on the step's stream --
@@ -521,6 +579,7 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               (prm->rule != GPAIR_RULE_GD_LINESEARCH || cudaMalloc(&S->Fg, N * 4) == cudaSuccess) &&
               cudaMalloc(&S->red, sizeof(double) * (2 * red_blocks() + 8)) == cudaSuccess &&
               cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
+              (adjoint_q_bytes(g, a) == 0 || cudaMalloc(&S->qbuf, adjoint_q_bytes(g, a)) == cudaSuccess) &&
               cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -544,7 +603,7 @@ void gpair_solver_destroy(gpair_solver* S) {
     if (!S) return;
     cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
     cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
-    cudaFree(S->fwd_scratch); cudaFree(S->status);
+    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status);
     for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
     delete S;
 }
@@ -599,7 +658,7 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
             return s;
         if ((e = launch_resid(S->y, b, S->delta, (float)(2.0 / (double)N), N, partial, res, st)) != cudaSuccess)
             return cuda_status(e);
-        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr)) !=
+        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr, S->qbuf)) !=
             GPAIR_OK)
             return s;
         const int tt = S->t + 1;
@@ -614,7 +673,7 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
         if ((s = run_forward(S->g, S->a, S->y, st, S->fwd_scratch, S->status, S->plan, ev ? ev + 1 : nullptr)) != GPAIR_OK)
             return s;
         if ((e = launch_resid(S->y, b, S->delta, 1.0f, N, partial, res, st)) != cudaSuccess) return cuda_status(e);
-        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr)) !=
+        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr, S->qbuf)) !=
             GPAIR_OK)
             return s;
         S->g.A = S->gx;

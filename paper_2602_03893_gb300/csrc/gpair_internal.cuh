@@ -82,6 +82,22 @@ struct PairRef {
     int n0;                  // nearest sample to the time of flight of c0
 };
 
+// Sub-sample expansion of the windowed pulse for a shared sigma.  A pair's window starts at the
+// first sample whose phase d0 satisfies d0 <= k sigma, so d0 lies in (k sigma - Delta, k sigma].
+// Writing d0 = dstar + e * Delta / 2 with dstar = k sigma - Delta / 2 and e in (-1, 1], the
+// pulse K(d) = d exp(-d^2 / 2 sigma^2) at window position m is the Taylor series
+//     K(d0 - m Delta) = sum_p c[m][p] e^p,  c[m][p] = K^(p)(dstar - m Delta) (Delta/2)^p / p!,
+// truncated after MOM_P terms (relative error < 1e-7 for Delta <= 0.75 sigma).  Positions
+// m < L are always inside the window; position L = floor(2 k sigma / Delta) is inside only when
+// d0 - L Delta >= -k sigma and is evaluated directly.
+constexpr int MOM_P = 8;
+constexpr int MOM_LMAX = 128;
+struct MomentTable {
+    int L;                       // positions always inside the window
+    float dstar, inv_half;       // reference phase and 2 / Delta
+    float c[MOM_LMAX][MOM_P];
+};
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
