@@ -185,7 +185,7 @@ adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ Mo
 __global__ void __launch_bounds__(ADJ_THREADS)
 adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const float* __restrict__ Q,
                   const __grid_constant__ MomentTable T, float* __restrict__ gA) {
-    __shared__ PairRef refs[ADJ_SC];
+    __shared__ PairRef refs2[2][ADJ_SC];
     const int64_t t = blockIdx.x;
     const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
     const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
@@ -202,14 +202,21 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
     const int L = T.L, Nt = a.Nt;
     const float LD = (float)L * Delta;
     KahanF kA;
-    for (int j0 = 0; j0 < a.Nd; j0 += ADJ_SC) {
+    // References are double-buffered: after each barrier the last warp forms the next chunk's
+    // FP64 references while the others already work on the current chunk.
+    if (warp == ADJ_THREADS / 32 - 1 && lane < min(ADJ_SC, a.Nd))
+        refs2[0][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * lane], a.xyz[3 * lane + 1], a.xyz[3 * lane + 2], a);
+    int cur = 0;
+    for (int j0 = 0; j0 < a.Nd; j0 += ADJ_SC, cur ^= 1) {
         const int nsc = min(ADJ_SC, a.Nd - j0);
-        if (warp == 0 && lane < nsc) {
-            const int j = j0 + lane;
-            refs[lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
-        }
         __syncthreads();
+        if (warp == ADJ_THREADS / 32 - 1 && j0 + ADJ_SC + lane < a.Nd) {
+            const int j = j0 + ADJ_SC + lane;
+            refs2[cur ^ 1][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        }
+        const PairRef* refs = refs2[cur];
         if (valid) {
+#pragma unroll 2
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
                 float invR, phi;
@@ -237,7 +244,6 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 kA.add(s * 0.5f * invR);
             }
         }
-        __syncthreads();
     }
     if (valid) gA[i] = kA.s;
 }

@@ -707,7 +707,7 @@ __host__ __device__ __forceinline__ size_t fwdm_warp_bytes(int TB, int LB, int L
            (((size_t)LB * 4 + 15) & ~(size_t)15);
 }
 
-__global__ void __launch_bounds__(FWD_THREADS, 2)
+__global__ void __launch_bounds__(FWD_THREADS, 3)
 fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
                   int2* __restrict__ rows, int LB, int TB, int* status, int use_tma,
                   const __grid_constant__ CUtensorMap tmap, const __grid_constant__ MomentTable T) {
@@ -780,7 +780,6 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
     const float reach = brick_radius(g.h) + ks;
     const float LD = (float)L * Delta;
     const int zlo = w - L;                 // first bin of the moment band
-    const unsigned lt_mask = (1u << lane) - 1u;
 
     PairRef refs;
     int t = 0;
@@ -851,14 +850,10 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                     const int nL = bin + L;
                     if (valid && dL >= -ks && nL >= w && nL <= n_hi)
                         atomicAdd(&xband[nL - w], wv[q] * dL * ex2_approx(dL * dL * c2));
-                    const unsigned grpmask = __match_any_sync(0xffffffffu, key[q]);
-                    const int before = __popc(grpmask & lt_mask);
-                    const int base = off[key[q]];
-                    __syncwarp();
-                    if (before == 0) off[key[q]] = base + __popc(grpmask);
-                    __syncwarp();
-                    rnk[q] = base + before;
+                    // rank within the bin (the order inside a bin only affects rounding)
+                    rnk[q] = valid ? atomicAdd(&off[key[q]], 1) : 0;
                 }
+                __syncwarp();
                 {   // exclusive scan of the bin counts
                     const int per = (NB + 31) / 32;
                     const int b0 = lane * per;
@@ -892,14 +887,21 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                     float M[MOM_P];
 #pragma unroll
                     for (int p = 0; p < MOM_P; ++p) M[p] = 0.f;
+                    static_assert(MOM_P == 8, "the power tree below is written for 8 moments");
+#pragma unroll 2
                     for (int i = start; i < end; ++i) {
                         const float2 rr = rec[i];
-                        float tt = rr.y;
-#pragma unroll
-                        for (int p = 0; p < MOM_P; ++p) {
-                            M[p] += tt;
-                            tt *= rr.x;
-                        }
+                        const float e1 = rr.x, wq = rr.y;
+                        const float e2 = e1 * e1, e4 = e2 * e2;
+                        const float e3 = e2 * e1, e5 = e4 * e1, e6 = e4 * e2, e7 = e4 * e3;
+                        M[0] += wq;
+                        M[1] = fmaf(wq, e1, M[1]);
+                        M[2] = fmaf(wq, e2, M[2]);
+                        M[3] = fmaf(wq, e3, M[3]);
+                        M[4] = fmaf(wq, e4, M[4]);
+                        M[5] = fmaf(wq, e5, M[5]);
+                        M[6] = fmaf(wq, e6, M[6]);
+                        M[7] = fmaf(wq, e7, M[7]);
                     }
                     float* zp = Z + (size_t)(ta + bb - zlo) * MOM_P;
 #pragma unroll

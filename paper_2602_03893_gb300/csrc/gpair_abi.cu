@@ -234,9 +234,10 @@ FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
     const int ngroups = (a.Nd + SPC - 1) / SPC;
     const int64_t target_S = ((int64_t)SM_COUNT_HINT * 4 * 4 + ngroups - 1) / ngroups;
     if (g.grid) {
-        // Compact blocks of bricks: start from 8 x 8 x 8 bricks and halve the longest side until
-        // there are enough CTAs; the band of a block is bounded by its diagonal.
-        int sb[3] = {std::min(8, g.ntx), std::min(8, g.nty), std::min(8, g.ntz)};
+        // Compact blocks of bricks: start from 4 x 4 x 8 bricks (a cube of 32 nodes a side) and
+        // halve the longest side until there are enough CTAs; the band of a block is bounded by its
+        // diagonal, and a short band keeps each warp's slab accumulators small.
+        int sb[3] = {std::min(4, g.ntx), std::min(4, g.nty), std::min(8, g.ntz)};
         const int nt[3] = {g.ntx, g.nty, g.ntz};
         const double ext[3] = {BX * (double)g.h, BY * (double)g.h, BZ * (double)g.h};
         auto count = [&] {
