@@ -8,7 +8,8 @@ grid, 1024 sensors, 4096 samples at 40 MHz -- with seeded synthetic data.
 Prints one JSON line (rank 0).  `value` is device time per iteration with inputs resident in
 HBM; `e2e` repeats the measurement through the public API with the measured signal copied from
 pinned host memory each step and the loss read back.  `roofline` uses the dominant kernel's own
-launch times (CUDA events on its stream, inside the timed region) against the FP32 issue rate.
+launch times (CUDA events on its stream, inside the timed region): the direct windowed
+evaluation's FP32 and MUFU work over that time, against the slower pipe's issue rate.
 `cpu_baseline` times the FP64 oracle on a bounded sensor sample (rank 0, N = 1 only).
 With N > 1 (torchrun) every rank runs an independent replica (the path is replicated, not
 sharded, on one-GPU machines): value = max-over-ranks time / (K * N).
@@ -36,7 +37,7 @@ UNIT = "s/iter"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-MUFU_LANES_PER_SM = 32          # ex2 throughput measured on this machine (lane-ops / clk / SM)
+MUFU_LANES_PER_SM = 32          # MUFU lanes per SM (ex2 measured at ~30 lane-ops / clk / SM)
 LAUNCHES_PER_STEP = 9           # npc, slab info, forward slab, slab reduce, resid, finish, tile info, adjoint, adam
 
 
@@ -66,17 +67,31 @@ def work_units(w):
     return pairs, samples
 
 
-# Algorithmic FP32 work: per sample-eval 3 lane-ops (power/recurrence step of the Gaussian,
-# the kernel value d*e, the accumulation), per pair 15 lane-ops (offset distance, phase,
-# window bounds, initial exponentials' arguments, weight A / 2R); 4 MUFU ops per pair.
-ALG_OPS_PER_SAMPLE = 3.0
-ALG_OPS_PER_PAIR = 15.0
-ALG_MUFU_PER_PAIR = 4.0
+# Algorithmic work of the direct windowed evaluation (the operator's definition): per sample-eval
+# 1 exponential (MUFU) and 4 FP32 ops (form d, scale d^2, d * A / 2R, accumulate; the adjoint adds
+# 1 FMA with delta); per pair 10 FP32 ops (offset distance, phase, window bounds, weight) and 2 MUFU
+# ops (rsqrt, rcp).  The bound is the slower pipe: T = max(F / P_fp32, X / P_mufu).  The kernels
+# factor the sample loop through sub-sample moments and execute fewer operations than this; the
+# fraction is the direct evaluation's work over the measured time.
+FP32_PER_SAMPLE = {"forward": 4.0, "adjoint": 5.0}
+FP32_PER_PAIR = 10.0
+MUFU_PER_SAMPLE = 1.0
+MUFU_PER_PAIR = 2.0
 
 
-def alg_ops(w):
+def alg_work(w, op):
+    """(FP32 lane-ops, MUFU lane-ops) of one operator application."""
     pairs, samples = work_units(w)
-    return ALG_OPS_PER_SAMPLE * samples + ALG_OPS_PER_PAIR * pairs
+    return (FP32_PER_SAMPLE[op] * samples + FP32_PER_PAIR * pairs,
+            MUFU_PER_SAMPLE * samples + MUFU_PER_PAIR * pairs)
+
+
+def kernel_names(w):
+    """Kernels the library launches for the two operators on this workload: the moment kernels
+    when the grid's shared sigma admits the sub-sample expansion (Delta <= sigma / 2)."""
+    if w.v / w.fs <= 0.5 * w.grid.sigma:
+        return {"forward": "fwd_moment_kernel", "adjoint": "adj_moment_kernel"}
+    return {"forward": "fwd_grid_kernel", "adjoint": "adj_kernel"}
 
 
 def src_hash(*names):
@@ -223,7 +238,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = workload(args.workload)
-    ns = max(1, min(w.Nd, args.cpu_sensors // 2))
+    # about 370 sensor-operators in total (a few minutes on 16 cores at the paper scale), spread over the
+    # warm-up and timed steps, at most cpu_sensors / 2 per step
+    ns = max(1, min(w.Nd, args.cpu_sensors // 2, 368 // max(1, args.warmup + args.steps)))
     vals = []
     for s in range(args.warmup + args.steps):
         r = cpu_baseline(w, ns, seed=100 + s)
@@ -321,25 +338,32 @@ def main():
 
     clocks = sampler.summary()
     pairs, samples = work_units(w)
-    ops = alg_ops(w)
     fwd_avg = fwd_ms / max(nrec, 1) / 1e3
     adj_avg = adj_ms / max(nrec, 1) / 1e3
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    kern = {"forward": {"kernel": "fwd_slab_kernel", "s_per_launch": fwd_avg, "achieved_Tops": ops / fwd_avg / 1e12,
-                        "frac": ops / fwd_avg / peak},
-            "adjoint": {"kernel": "adj_kernel", "s_per_launch": adj_avg, "achieved_Tops": ops / adj_avg / 1e12,
-                        "frac": ops / adj_avg / peak}}
+    p_fp32 = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    p_mufu = SM_COUNT * MUFU_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    names = kernel_names(w)
+    kern = {}
+    for op, t in (("forward", fwd_avg), ("adjoint", adj_avg)):
+        F, X = alg_work(w, op)
+        t_fp32, t_mufu = F / p_fp32, X / p_mufu
+        pipe = "fp32" if t_fp32 >= t_mufu else "mufu"
+        ops, peak = (F, p_fp32) if pipe == "fp32" else (X, p_mufu)
+        kern[op] = {"kernel": names[op], "s_per_launch": t, "bound_pipe": pipe, "t_bound_s": max(t_fp32, t_mufu),
+                    "alg_fp32_ops": F, "alg_mufu_ops": X, "achieved": ops / t / 1e12, "peak": peak / 1e12,
+                    "frac": ops / t / peak}
     dom = "forward" if fwd_avg >= adj_avg else "adjoint"
     src = src_hash("forward.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
     tr = profiled_traffic(kern[dom]["kernel"], src)
-    mufu_bound = ALG_MUFU_PER_PAIR * pairs / (SM_COUNT * MUFU_LANES_PER_SM * SM_MAX_MHZ * 1e6)
-    roofline = {"bound": "alu", "achieved": ops / (fwd_avg if dom == "forward" else adj_avg) / 1e12,
-                "peak": peak / 1e12, "unit": "T FP32 lane-ops/s", "frac": kern[dom]["frac"],
-                "traffic": tr, "kernel": kern[dom]["kernel"],
-                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
-                "alg_ops_per_launch": ops, "mufu_bound_s": mufu_bound, "kernels": kern}
+    kd = kern[dom]
+    roofline = {"bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": "T lane-ops/s (" + ("FP32" if kd["bound_pipe"] == "fp32" else "MUFU") + ")",
+                "frac": kd["frac"], "traffic": tr, "kernel": kd["kernel"],
+                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 / {MUFU_LANES_PER_SM} MUFU lanes x "
+                              f"{SM_MAX_MHZ:.0f} MHz (max SM clock); not in the measured-peaks file",
+                "kernels": kern}
     if clocks.get("sm_mhz"):
-        roofline["frac_at_measured_clock"] = kern[dom]["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
+        roofline["frac_at_measured_clock"] = kd["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

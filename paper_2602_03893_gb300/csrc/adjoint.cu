@@ -200,7 +200,7 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
     const float ks = a.k * g.sigma, Delta = a.Delta, invDelta = a.invDelta;
     const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
     const int L = T.L, Nt = a.Nt;
-    const float LD = (float)L * Delta;
+    const float ED = (float)T.E * Delta;
     KahanF kA;
     // References are double-buffered: after each barrier the last warp forms the next chunk's
     // FP64 references while the others already work on the current chunk.
@@ -236,10 +236,12 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 s = fmaf(s, e, q0.z);
                 s = fmaf(s, e, q0.y);
                 s = fmaf(s, e, q0.x);
-                const float dL = d0 - LD;              // window position L, inside only at the edge
-                if (dL >= -ks) {
-                    const int n = b + L;
-                    if (n >= 0 && n < Nt) s = fmaf(delta[(size_t)(j0 + q) * Nt + n] * dL, ex2_approx(dL * dL * c2), s);
+                const float dE = d0 - ED;              // edge position E: rare direct correction
+                const float sg = edge_sign(T, dE, ks);
+                if (sg != 0.f) {
+                    const int n = b + T.E;
+                    if (n >= 0 && n < Nt)
+                        s = fmaf(sg * delta[(size_t)(j0 + q) * Nt + n] * dE, ex2_approx(dE * dE * c2), s);
                 }
                 kA.add(s * 0.5f * invR);
             }

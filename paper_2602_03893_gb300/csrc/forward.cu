@@ -698,10 +698,28 @@ fwd_grid_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
 // pair is reduced to its window-start bin b and offset e: the slab keeps, per bin, the moments
 //     Z_p[b] = sum over the slab's pairs starting at b of w e^p     (p < MOM_P)
 // and the signal is their correlation with the table, y[n] = sum_{m<L} sum_p c[m][p] Z_p[n - m],
-// plus the few pairs whose window also holds position L (evaluated directly).  Lanes own bins:
+// plus the direct edge terms of the few pairs the table misses at position E.  Lanes own bins:
 // a lane sums the moments of its bin's records in registers and adds them into the slab's
-// moment band; no atomics except the rare direct terms.
+// moment band (moment-major, so a warp's adds hit consecutive banks); no atomics except the
+// ranks within a bin and the rare direct terms.
+//
+// Tiles stream through a ring of FWDM_RING shared buffers.  Each slot has a "full" barrier
+// (completed by the TMA's byte count, or by the arrive of the warp that loaded it with plain
+// loads) and a release counter; the last of the CTA's warps to release a slot refills it.  The
+// warps (one sensor each) thus drift apart by up to FWDM_RING tiles instead of meeting at a CTA
+// barrier every tile.
+constexpr int FWDM_RING = 4;
+struct FwdMomSmem {
+    float tileA[FWDM_RING][TILE];
+    uint64_t full[FWDM_RING];
+    int released[FWDM_RING];     // release count of the slot, all phases (never reset)
+    int issued[FWDM_RING];       // last tile copied into the slot by TMA (-1: none)
+    int abort;
+};
+constexpr size_t FWDM_HDR = (sizeof(FwdMomSmem) + 127) & ~(size_t)127;
 
+// Per-warp shared memory: sorted records (e, w) [TILE] | bin offsets [TB + 2] | moment band
+// [MOM_P][LB + L] | direct-term band [LB].
 __host__ __device__ __forceinline__ size_t fwdm_warp_bytes(int TB, int LB, int L) {
     return (size_t)TILE * 8 + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15) + (size_t)(LB + L) * MOM_P * 4 +
            (((size_t)LB * 4 + 15) & ~(size_t)15);
@@ -711,15 +729,18 @@ __global__ void __launch_bounds__(FWD_THREADS, 3)
 fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
                   int2* __restrict__ rows, int LB, int TB, int* status, int use_tma,
                   const __grid_constant__ CUtensorMap tmap, const __grid_constant__ MomentTable T) {
+    static_assert(BX == 8 && BY == 8 && BZ == 4 && TILE == 256,
+                  "lane offsets below assume lane + 32 q -> (lane & 7, (lane >> 3) + 4 (q & 1), q >> 1)");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    FwdGridSmem& S = *reinterpret_cast<FwdGridSmem*>(smem_raw);
+    FwdMomSmem& S = *reinterpret_cast<FwdMomSmem*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = T.L;
-    unsigned char* wbase = smem_raw + FWDG_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L);
+    const int ZS = LB + L;                 // bins of the moment band
+    unsigned char* wbase = smem_raw + FWDM_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L);
     float2* rec = reinterpret_cast<float2*>(wbase);
     int* off = reinterpret_cast<int*>(wbase + (size_t)TILE * 8);
     float* Z = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(off) + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15));
-    float* xband = Z + (size_t)(LB + L) * MOM_P;
+    float* xband = Z + (size_t)ZS * MOM_P;
 
     const int slab = blockIdx.y;
     const int j = blockIdx.x * FWD_SPC + warp;
@@ -751,54 +772,66 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
         n_hi = w + LB - 1;
     }
     if (lane == 0 && has_sensor) rows[row] = make_int2(w, active ? min(LB, a.Nt - w) : 0);
-    if (threadIdx.x == 0) S.abort = 0;
-    const bool tma = use_tma != 0;
-    if (tma && threadIdx.x == 0) {
-        mbar_init(&S.mbar[0], 1);
-        mbar_init(&S.mbar[1], 1);
+    if (threadIdx.x == 0) {
+        S.abort = 0;
+        for (int b = 0; b < FWDM_RING; ++b) {
+            S.released[b] = 0;
+            S.issued[b] = -1;
+            mbar_init(&S.full[b], 1);
+        }
         fence_mbar_init();
     }
-    for (int q = lane; q < (LB + L) * MOM_P; q += 32) Z[q] = 0.f;
+    for (int q = lane; q < ZS * MOM_P; q += 32) Z[q] = 0.f;
     for (int q = lane; q < LB; q += 32) xband[q] = 0.f;
     __syncthreads();
 
-    auto issue = [&](int TT) {
+    const bool tma = use_tma != 0;
+    // Warp-cooperative fill of the slot of tile TT: one TMA copy issued by lane 0, or plain loads
+    // by the warp's lanes followed by one release arrive.
+    auto fill = [&](int TT) {
+        const int b = TT % FWDM_RING;
         int tx, ty, tz;
         slab_brick(sl, TT, tx, ty, tz);
-        const int b = TT & 1;
-        mbar_arrive_expect_tx(&S.mbar[b], TILE * sizeof(float));
-        tma_load_3d(&S.tileA[b][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.mbar[b]);
-    };
-    if (tma && threadIdx.x == 0) {
-        if (nTiles > 0) issue(0);
-        if (nTiles > 1) issue(1);
-    }
-
-    const float Delta = a.Delta, invDelta = a.invDelta;
-    const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
-    const float ks = a.k * g.sigma;
-    const float reach = brick_radius(g.h) + ks;
-    const float LD = (float)L * Delta;
-    const int zlo = w - L;                 // first bin of the moment band
-
-    PairRef refs;
-    int t = 0;
-    for (; t < nTiles; ++t) {
-        const int b = t & 1;
         if (tma) {
-            bool ok = mbar_wait(&S.mbar[b], (uint32_t)((t >> 1) & 1));
-            if (!ok) S.abort = 1;
-            __syncthreads();
-            if (S.abort) break;
+            if (lane == 0) {
+                S.issued[b] = TT;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect_tx(&S.full[b], TILE * sizeof(float));
+                tma_load_3d(&S.tileA[b][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.full[b]);
+            }
         } else {
-            int tx, ty, tz;
-            slab_brick(sl, t, tx, ty, tz);
-            for (int q = threadIdx.x; q < TILE; q += FWD_THREADS) {
+            for (int q = lane; q < TILE; q += 32) {
                 const int gx = tx * BX + (q & (BX - 1)), gy = ty * BY + ((q / BX) & (BY - 1)), gz = tz * BZ + q / (BX * BY);
                 const bool ok = gx < g.nx && gy < g.ny && gz < g.nz;
                 S.tileA[b][q] = ok ? g.A[((int64_t)gz * g.ny + gy) * g.nx + gx] : 0.f;
             }
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.full[b]);
+        }
+    };
+    if (warp == 0)
+        for (int TT = 0; TT < FWDM_RING && TT < nTiles; ++TT) fill(TT);
+
+    const float Delta = a.Delta, invDelta = a.invDelta;
+    const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
+    const float ks = a.k * g.sigma;
+    const float rad = brick_radius(g.h);
+    const float ED = (float)T.E * Delta;
+    const int zlo = w - L;                 // first bin of the moment band
+    // this lane's lattice offsets from the brick centre (Gaussian l = lane + 32 q)
+    const float h = g.h;
+    const float ox = ((float)(lane & 7) - 0.5f * (BX - 1)) * h;
+    const float oy0 = ((float)(lane >> 3) - 0.5f * (BY - 1)) * h;
+    const float oy1 = ((float)((lane >> 3) + 4) - 0.5f * (BY - 1)) * h;
+
+    PairRef refs;
+    int t = 0;
+    bool ok = true;
+    for (; t < nTiles; ++t) {
+        const int b = t % FWDM_RING;
+        if (!mbar_wait(&S.full[b], (uint32_t)((t / FWDM_RING) & 1))) {
+            ok = false;
+            break;
         }
         if (active) {
             if ((t & 31) == 0 && t + lane < nTiles) {
@@ -815,9 +848,9 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
             r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
             r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
             r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
-            // window-start bins this tile can produce that reach this slab's samples
-            int ta = r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2;
-            int tb = r.n0 + (int)ceilf((r.phi0 + reach) * invDelta) + 2;
+            // window-start bins of the brick: its phases lie within rad of phi0
+            int ta = r.n0 + (int)floorf((r.phi0 - rad - ks) * invDelta) - 2;
+            int tb = r.n0 + (int)ceilf((r.phi0 + rad - ks) * invDelta) + 2;
             ta = max(ta, zlo);
             tb = min(tb, n_hi);
             if (ta <= tb) {
@@ -829,15 +862,19 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                 }
                 for (int q = lane; q <= NB; q += 32) off[q] = 0;
                 __syncwarp();
+                // num = 2 (c0 - s) . delta + |delta|^2, separable over the lane's offsets
+                const float ax = ox * (2.f * r.v0x + ox);
+                const float ay0 = oy0 * (2.f * r.v0y + oy0), ay1 = oy1 * (2.f * r.v0y + oy1);
                 int key[TILE / 32], rnk[TILE / 32];
                 float ev[TILE / 32], wv[TILE / 32];
 #pragma unroll
                 for (int q = 0; q < TILE / 32; ++q) {
                     const int l = lane + 32 * q;
                     const float Ai = S.tileA[b][l];
-                    float dx, dy, dz, invR, phi;
-                    brick_offset(l, g.h, dx, dy, dz);
-                    pair_phase_fast(r, dx, dy, dz, invR, phi);
+                    const float oz = ((float)(q >> 1) - 0.5f * (BZ - 1)) * h;
+                    const float num = (ax + ((q & 1) ? ay1 : ay0)) + oz * (2.f * r.v0z + oz);
+                    float invR, phi;
+                    pair_phase_num(r, num, invR, phi);
                     const int m_lo = (int)ceilf((phi - ks) * invDelta);
                     const int bin = r.n0 + m_lo;
                     const bool valid = Ai != 0.f && bin >= ta && bin <= tb;
@@ -845,11 +882,12 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                     const float d0 = fmaf(-(float)m_lo, Delta, phi);
                     ev[q] = (d0 - T.dstar) * T.inv_half;
                     wv[q] = Ai * 0.5f * invR;
-                    // window position L: inside only at the window edge; added directly
-                    const float dL = d0 - LD;
-                    const int nL = bin + L;
-                    if (valid && dL >= -ks && nL >= w && nL <= n_hi)
-                        atomicAdd(&xband[nL - w], wv[q] * dL * ex2_approx(dL * dL * c2));
+                    // edge position E: the rare pairs the table does not account for, directly
+                    const float dE = d0 - ED;
+                    const int nE = bin + T.E;
+                    const float sg = edge_sign(T, dE, ks);
+                    if (valid && sg != 0.f && nE >= w && nE <= n_hi)
+                        atomicAdd(&xband[nE - w], sg * wv[q] * dE * ex2_approx(dE * dE * c2));
                     // rank within the bin (the order inside a bin only affects rounding)
                     rnk[q] = valid ? atomicAdd(&off[key[q]], 1) : 0;
                 }
@@ -903,23 +941,34 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                         M[6] = fmaf(wq, e6, M[6]);
                         M[7] = fmaf(wq, e7, M[7]);
                     }
-                    float* zp = Z + (size_t)(ta + bb - zlo) * MOM_P;
+                    float* zp = Z + (ta + bb - zlo);
 #pragma unroll
-                    for (int p = 0; p < MOM_P; ++p) zp[p] += M[p];
+                    for (int p = 0; p < MOM_P; ++p) zp[(size_t)p * ZS] += M[p];
                 }
                 __syncwarp();
             }
         }
-        __syncthreads();   // every warp is done with buffer b
-        if (tma && threadIdx.x == 0 && t + 2 < nTiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(t + 2);
+        // release the slot; the warp that releases it last refills it with tile t + FWDM_RING
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = (atomicAdd(&S.released[b], 1) + 1) % FWD_SPC == 0;
+            if (last) __threadfence_block();
         }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last && t + FWDM_RING < nTiles) fill(t + FWDM_RING);
     }
-    if (t < nTiles) {      // a bounded wait ran out
+    if (!ok && lane == 0) {   // a bounded wait ran out
         set_status(status, DEV_TIMEOUT);
+        S.abort = 1;
+    }
+    __syncthreads();
+    if (S.abort) {
+        // wait (bounded) for the last copy issued into each slot before the CTA exits
         if (tma && threadIdx.x == 0)
-            for (int U = t; U < nTiles && U < t + 2; ++U) mbar_wait(&S.mbar[U & 1], (uint32_t)((U >> 1) & 1));
+            for (int b = 0; b < FWDM_RING; ++b)
+                if (S.issued[b] >= 0) mbar_wait(&S.full[b], (uint32_t)((S.issued[b] / FWDM_RING) & 1));
         return;
     }
     if (active) {
@@ -927,11 +976,11 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
         const int wend = min(a.Nt, w + LB);
         for (int q = lane; q < wend - w; q += 32) {
             float y = xband[q];
-            const float* zb = Z + (size_t)(q + L) * MOM_P;   // bin n = w + q sits at index q + L
+            const float* zb = Z + q + L;       // bin n = w + q sits at index q + L
             for (int m = 0; m < L; ++m) {
-                const float* zm = zb - (size_t)m * MOM_P;
+                const float* zm = zb - m;
 #pragma unroll
-                for (int p = 0; p < MOM_P; ++p) y = fmaf(T.c[m][p], zm[p], y);
+                for (int p = 0; p < MOM_P; ++p) y = fmaf(T.c[m][p], zm[(size_t)p * ZS], y);
             }
             prow[q] = y;
         }
@@ -1002,11 +1051,14 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
     dim3 grid((a.Nd + FWD_SPC - 1) / FWD_SPC, S);
     cudaError_t e;
     if (g.grid && binned && mom) {
-        const size_t msm = FWDG_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TB, LB, mom->L);
+        // window-start bins of one brick: phases within its radius of phi0, so at most
+        // 2 rad / Delta + 7 bins (floor/ceil and the -2/+2 margins)
+        const int TBm = ((int)std::ceil(2.0 * brick_radius(g.h) * a.invDelta) + 8 + 3) & ~3;
+        const size_t msm = FWDM_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TBm, LB, mom->L);
         if (msm <= 227 * 1024) {
             e = cudaFuncSetAttribute(fwd_moment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
             if (e != cudaSuccess) return e;
-            fwd_moment_kernel<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TB, status, tmap != nullptr,
+            fwd_moment_kernel<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TBm, status, tmap != nullptr,
                                                               *(tmap ? tmap : &null_tmap()), *mom);
             return cudaGetLastError();
         }

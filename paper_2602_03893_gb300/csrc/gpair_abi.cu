@@ -204,9 +204,12 @@ void grid_plan_from_blocks(FwdPlan& p, const GaussDev& g, const ArrDev& a, const
     int64_t s = 1;
     for (int q = 0; q < 3; ++q) s *= (nt[q] + sb[q] - 1) / sb[q];
     p.S = (int)s;
-    const double dx = sb[0] * ext[0], dy = sb[1] * ext[1], dz = sb[2] * ext[2];
+    // span of the block's lattice centres (B sb - 1 spacings per axis)
+    const double dx = sb[0] * ext[0] - g.h, dy = sb[1] * ext[1] - g.h, dz = sb[2] * ext[2] - g.h;
     const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
-    p.LB = ((int)std::ceil((diag + 2.0 * a.k * g.sigma) * a.invDelta) + 16 + 3) & ~3;
+    // n_lo, n_hi of a (slab, sensor) are floor/ceil of the band edges -/+ 2 samples; with the inclusive
+    // end and the 4-alignment of the band start the band spans at most (diag + 2 k sigma) / Delta + 10.
+    p.LB = ((int)std::ceil((diag + 2.0 * a.k * g.sigma) * a.invDelta) + 10 + 3) & ~3;
     p.PL = p.LB;
     const double reach = brick_radius(g.h) + a.k * g.sigma;
     p.TB = ((int)std::ceil(2.0 * reach * a.invDelta) + 8 + 31) & ~31;
@@ -331,10 +334,16 @@ bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
     if (!g.grid) return false;
     const double s = g.sigma, Delta = (double)a.Delta, k = a.k;
     const double X = 2.0 * k * s / Delta;
-    const int L = (int)std::floor(X);
-    if (L < 1 || L > MOM_LMAX || Delta > 0.5 * s) return false;
+    const int E = (int)std::floor(X);
+    // position E is inside the window for a fraction X - E of the pairs: include it in the
+    // expansion when that is the majority, so that the direct correction stays rare
+    const int edge_in = (X - E > 0.5) ? 1 : 0;
+    const int L = E + edge_in;
+    if (E < 1 || L > MOM_LMAX || Delta > 0.5 * s) return false;
     const double dstar = k * s - 0.5 * Delta;
     T.L = L;
+    T.E = E;
+    T.edge_in = edge_in;
     T.dstar = (float)dstar;
     T.inv_half = (float)(2.0 / Delta);
     for (int m = 0; m < MOM_LMAX; ++m)

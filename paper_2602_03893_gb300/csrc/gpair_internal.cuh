@@ -88,15 +88,27 @@ struct PairRef {
 // pulse K(d) = d exp(-d^2 / 2 sigma^2) at window position m is the Taylor series
 //     K(d0 - m Delta) = sum_p c[m][p] e^p,  c[m][p] = K^(p)(dstar - m Delta) (Delta/2)^p / p!,
 // truncated after MOM_P terms (relative error < 1e-7 for Delta <= 0.75 sigma).  Positions
-// m < L are always inside the window; position L = floor(2 k sigma / Delta) is inside only when
-// d0 - L Delta >= -k sigma and is evaluated directly.
+// m < E = floor(2 k sigma / Delta) are always inside the window, position E is inside when
+// d0 - E Delta >= -k sigma (for a fraction 2 k sigma / Delta - E of the pairs), later positions
+// never.  The table covers positions m < L: L = E + 1 when position E is inside for most pairs
+// (edge_in = 1; the pairs for which it is outside subtract its term, evaluated directly), else
+// L = E (the pairs for which it is inside add its term).
 constexpr int MOM_P = 8;
 constexpr int MOM_LMAX = 128;
 struct MomentTable {
-    int L;                       // positions always inside the window
+    int L;                       // positions covered by the expansion
+    int E;                       // edge position
+    int edge_in;                 // 1: the table covers position E
     float dstar, inv_half;       // reference phase and 2 / Delta
     float c[MOM_LMAX][MOM_P];
 };
+
+// Direct-term correction of a pair at the edge position E, given dE = d0 - E Delta: the signed
+// factor (0 when the table already accounts for the pair) that multiplies w dE exp(-dE^2/2s^2).
+__device__ __forceinline__ float edge_sign(const MomentTable& T, float dE, float ks) {
+    const bool inside = dE >= -ks;
+    return inside == (T.edge_in != 0) ? 0.f : (inside ? 1.f : -1.f);
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -153,6 +165,16 @@ __device__ __forceinline__ void pair_phase(const PairRef& r, float dx, float dy,
 // Same as pair_phase with hardware reciprocal square root and reciprocal (a few ulp): returns
 // 1/R (for the weight A/2R) and the phase.  The relative error of 1/R is ~1e-7; the phase
 // correction R - R0 (at most a few mm) keeps an absolute error of ~1e-10 m.
+// Second half of pair_phase_fast, from num = R^2 - R0^2 = 2 (c0 - s) . delta + |delta|^2.
+__device__ __forceinline__ void pair_phase_num(const PairRef& r, float num, float& invR, float& phi) {
+    const float R2 = fmaf(r.R0, r.R0, num);
+    invR = rsqrtf(R2);
+    const float R = R2 * invR;
+    float rc;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(r.R0 + R));
+    phi = fmaf(num, rc, r.phi0);
+}
+
 __device__ __forceinline__ void pair_phase_fast(const PairRef& r, float dx, float dy, float dz,
                                                 float& invR, float& phi) {
     const float num = dx * (2.f * r.v0x + dx) + dy * (2.f * r.v0y + dy) + dz * (2.f * r.v0z + dz);
@@ -185,6 +207,12 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Plain arrive (release semantics at CTA scope): completes a phase of a count-1 barrier after
+// the calling thread's (and, after a __syncwarp, its warp's) shared-memory stores.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
 }
 
 // Returns true when the phase with the given parity has completed, false after WAIT_LIMIT

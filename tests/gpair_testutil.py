@@ -85,3 +85,12 @@ def assert_signal_parity(y_gpu, y_ora, amb, tol=1e-5):
     assert np.all(np.isfinite(y_gpu))
     assert err <= bound, f"|err| {err:.3e} > bound {bound:.3e} (rel {err / max(np.linalg.norm(y_ora), 1e-300):.3e})"
     return err / max(np.linalg.norm(y_ora), 1e-300)
+
+
+def edge_workload(sigma_scale):
+    """Tiny geometry with sigma = sigma_scale * h: 2 k sigma / Delta = 32 sigma_scale, so the
+    window's edge position E = floor(2 k sigma / Delta) is inside for a fraction 0.32 (1.01) or
+    0.64 (1.02) of the pairs."""
+    g = synth.centred_grid(16, 16, 16, 0.2e-3, sigma=0.2e-3 * sigma_scale)
+    A = np.random.default_rng(11).uniform(0.0, 1.0, g.M).astype(np.float32)
+    return synth.Workload("edge", g, synth.cap_sensors(128, 20e-3, 180.0), 1024, A=A)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpair_testutil import TAU, gpu_adjoint, gpu_forward, oracle_gaussians, rel_l2
+from gpair_testutil import TAU, edge_workload, gpu_adjoint, gpu_forward, oracle_gaussians, rel_l2
 from paper_2602_03893_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,13 @@ def test_tiny_amplitude_gradient(k):
     w = synth.tiny(1)
     delta = np.random.default_rng(2).normal(size=(w.Nd, w.Nt)).astype(np.float32)
     _check(w, delta, full=False, k=k)
+
+
+@pytest.mark.parametrize("sigma_scale", [1.01, 1.02])
+def test_window_edge_position_in_and_out_of_expansion(sigma_scale):
+    w = edge_workload(sigma_scale)
+    delta = np.random.default_rng(12).normal(size=(w.Nd, w.Nt)).astype(np.float32)
+    _check(w, delta, full=False, A=w.A)
 
 
 def test_adjoint_identity_on_gpu():

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpair_testutil import TAU, assert_signal_parity, gpu_forward, oracle_gaussians, rel_l2
+from gpair_testutil import TAU, assert_signal_parity, edge_workload, gpu_forward, oracle_gaussians, rel_l2
 from paper_2602_03893_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +38,16 @@ def test_tiny_dense_amplitudes():
     w = synth.tiny(1)
     A = np.random.default_rng(8).uniform(0.0, 1.0, w.M).astype(np.float32)
     _check(w, A=A)
+
+
+@pytest.mark.parametrize("sigma_scale", [1.01, 1.02])
+def test_window_edge_position_in_and_out_of_expansion(sigma_scale):
+    """The sub-sample expansion covers the edge position E when it is inside the window for most
+    pairs and corrects the others directly, else leaves E to the direct term; one case each."""
+    w = edge_workload(sigma_scale)
+    X = 2 * w.k * w.grid.sigma * w.fs / w.v
+    assert (X % 1.0 > 0.5) == (sigma_scale > 1.015)
+    _check(w)
 
 
 def test_free_gaussians_per_gaussian_sigma():
