@@ -362,6 +362,9 @@ def main():
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 / {MUFU_LANES_PER_SM} MUFU lanes x "
                               f"{SM_MAX_MHZ:.0f} MHz (max SM clock); not in the measured-peaks file",
                 "kernels": kern}
+    # both operators of the iteration together: their bounds over their measured times
+    roofline["fwd_plus_adj_frac"] = ((kern["forward"]["t_bound_s"] + kern["adjoint"]["t_bound_s"]) /
+                                     (fwd_avg + adj_avg))
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = kd["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
 
