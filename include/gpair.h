@@ -201,6 +201,13 @@ const char* gpair_status_string(gpair_status s);
 gpair_status gpair_last_device_status(void* stream);
 /* Frees the scratch pool of every stream on the current device. */
 void gpair_release_scratch(void);
+
+/* gpair_wait_selftest -- exercises the failure-detection path of the bounded waits.  Launches one
+ * warp that waits on a shared-memory barrier nothing completes, giving up after `polls` polls
+ * (1 <= polls <= 2^20, else GPAIR_ERR_INVALID_ARG, nothing launched); the kernel records a timeout
+ * in the stream's device status word and returns normally, leaving the context usable.  The next
+ * gpair_last_device_status(stream) returns GPAIR_ERR_TIMEOUT.  The paper has no counterpart. */
+gpair_status gpair_wait_selftest(int polls, void* stream);
 /* Library version string. */
 const char* gpair_version(void);
 

@@ -27,7 +27,7 @@ EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_vox
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
-           "gpair_version")
+           "gpair_wait_selftest", "gpair_version")
 
 
 class GpairError(RuntimeError):
@@ -86,6 +86,7 @@ def load(path: str | None = None):
         lib.gpair_last_device_status.argtypes = [P]
         lib.gpair_release_scratch.argtypes = []
         lib.gpair_release_scratch.restype = None
+        lib.gpair_wait_selftest.argtypes = [c_int, P]
         lib.gpair_version.restype = ctypes.c_char_p
         _lib = lib
     return _lib
@@ -240,6 +241,12 @@ def gpair_last_device_status(stream=None) -> int:
 
 def gpair_release_scratch() -> None:
     load().gpair_release_scratch()
+
+
+def gpair_wait_selftest(polls: int, stream=None) -> None:
+    """Launch the bounded-wait self-test (a wait nothing completes, given up after `polls` polls);
+    the next gpair_last_device_status reports the timeout."""
+    _check("gpair_wait_selftest", load().gpair_wait_selftest(int(polls), _stream(stream)))
 
 
 def gpair_version() -> str:

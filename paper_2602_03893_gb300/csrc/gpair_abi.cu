@@ -28,6 +28,7 @@ size_t adj_moment_q_bytes(const ArrDev& a, int L);
 cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const float* delta, float* gA,
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
+cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t st);
 cudaError_t launch_resid(const float* y, const float* b, float* delta, float scale, int64_t n, double* partial,
                          double* out, cudaStream_t st);
 cudaError_t launch_reduce2(const float* a, const float* b, const float* c, int64_t n, double* partial, double* out,
@@ -503,6 +504,15 @@ gpair_status gpair_last_device_status(void* stream) {
     if (h == DEV_TIMEOUT) return GPAIR_ERR_TIMEOUT;
     if (h == DEV_CAPACITY) return GPAIR_ERR_UNSUPPORTED;
     return GPAIR_OK;
+}
+
+gpair_status gpair_wait_selftest(int polls, void* stream) {
+    if (polls < 1 || polls > (1 << 20)) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* status = nullptr;
+    gpair_status s = get_scratch(st, 0, nullptr, &status);
+    if (s != GPAIR_OK) return s;
+    return cuda_status(launch_wait_selftest((uint32_t)polls, status, st));
 }
 
 void gpair_release_scratch(void) {

@@ -163,4 +163,27 @@ cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M
 
 int red_blocks() { return RED_BLOCKS; }
 
+// Failure-detection self-test: one warp waits on a shared-memory barrier that nothing completes,
+// with a bound of `polls` polls; the wait gives up, the timeout goes into the status word and the
+// kernel returns normally (no trap, nothing in flight).
+__global__ void wait_selftest_kernel(uint32_t polls, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_n(&bar, 0u, polls);
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (!ok) set_status(status, DEV_TIMEOUT);
+        mbar_inval(&bar);
+    }
+}
+
+cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(polls, status);
+    return cudaGetLastError();
+}
+
 }  // namespace gp

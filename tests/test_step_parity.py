@@ -97,3 +97,22 @@ def test_reduce_f64_against_numpy():
     ref1 = float(np.sum(a.astype(np.float64) * c))
     assert abs(o[0] - ref0) <= 1e-12 * ref0
     assert abs(o[1] - ref1) <= 1e-12 * np.sum(np.abs(a.astype(np.float64) * c))
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: a device wait that nothing completes gives up after its
+    bound, the host reads the timeout from the status word, and the next operator call runs
+    normally on the same context."""
+    import torch
+
+    from gpair_testutil import gpu_forward
+
+    assert _lib.gpair_last_device_status() == 0
+    _lib.gpair_wait_selftest(4096)
+    torch.cuda.synchronize()
+    assert _lib.gpair_last_device_status() == 4            # GPAIR_ERR_TIMEOUT
+    assert _lib.gpair_last_device_status() == 0            # reading clears the word
+    w = synth.tiny(1)
+    assert np.abs(gpu_forward(w)).max() > 0
+    with pytest.raises(_lib.GpairError):
+        _lib.gpair_wait_selftest(0)                         # rejected on the host, nothing launched
