@@ -202,6 +202,25 @@ gpair_status gpair_last_device_status(void* stream);
 /* Frees the scratch pool of every stream on the current device. */
 void gpair_release_scratch(void);
 
+/* ---- The paper's own discretised operator (Methods, adaptive supersampling alignment;
+ * Algorithm 1), for grid Gaussians sharing one width sigma.
+ *
+ * Grid: N_half = ceil(3 sigma / (v / fs)), alpha = max(1, ceil(((n_min - 1) / 2) / N_half)) (the
+ * paper uses n_min = 25), K = alpha N_half; evaluated in double from the given float arguments.
+ * Forward: each pair's time of flight is snapped to the fine sample
+ * k_ij = floor((r_ij / v - t0) alpha fs + 1/2), its mass A_i / r_ij accumulates there when
+ * 0 <= k_ij < alpha N_t, the impulse line is convolved with h[k] = (1/2) d exp(-d^2 / 2 sigma^2),
+ * d = -v k / (alpha fs), |k| <= K, and decimated: y_j[n] = sum_i (A_i / r_ij) h[alpha n - k_ij].
+ * arr->window_k is not used (the pulse support is the paper's 3-sigma rule, N_half samples).
+ * Adjoint: gA_i = sum_j (1 / r_ij) sum_n h[alpha n - k_ij] delta_j[n], the exact transpose.
+ * Layouts as gpair_forward / gpair_adjoint; gA has M entries.  Errors: GPAIR_ERR_UNSUPPORTED for
+ * free-centre Gaussians, K > 256 or alpha N_t >= 2^30; GPAIR_ERR_INVALID_ARG for n_min < 1 or
+ * NULL buffers.  Asynchronous on `stream`; scratch from the library's per-stream pool (the
+ * adjoint's correlated residual: N_d alpha N_t floats). */
+gpair_status gpair_assa_forward(const gpair_gaussians* g, const gpair_array* arr, int n_min, float* y, void* stream);
+gpair_status gpair_assa_adjoint(const gpair_gaussians* g, const gpair_array* arr, int n_min, const float* delta,
+                                float* gA, void* stream);
+
 /* gpair_wait_selftest -- exercises the failure-detection path of the bounded waits.  Launches one
  * warp that waits on a shared-memory barrier nothing completes, giving up after `polls` polls
  * (1 <= polls <= 2^20, else GPAIR_ERR_INVALID_ARG, nothing launched); the kernel records a timeout

@@ -64,6 +64,15 @@ def _load():
         _lib.ora_ir.argtypes = [i64, dp, dp, dp, dp, i32, dp, f64, f64, f64, i32, f64,
                                 dp, i32, i32, i32, f64, f64, f64, i32, f64, f64, f64, f64,
                                 dp, dp, dp]
+        _lib.ora_assa_params.restype = None
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.ora_assa_params.argtypes = [f64, f64, f64, i32, ip, ip, ip]
+        _lib.ora_assa_forward.restype = None
+        _lib.ora_assa_forward.argtypes = [i64, dp, dp, dp, dp, f64, i32, dp, f64, f64, f64, i32, i32, f64,
+                                          dp, dp]
+        _lib.ora_assa_adjoint.restype = None
+        _lib.ora_assa_adjoint.argtypes = [i64, dp, dp, dp, f64, i32, dp, f64, f64, f64, i32, i32, dp, f64,
+                                          dp, dp]
         _lib.ora_set_threads.argtypes = [i32]
         _lib.ora_get_threads.restype = i32
     return _lib
@@ -176,6 +185,42 @@ def adjoint(g: Gaussians, sensors, v, fs, t0, Nt, delta, k=3.0, want=("A",), tau
     if want_amb:
         out["ambA"], out["ambC"], out["ambS"] = amb
     return out
+
+
+def assa_params(sigma, v, fs, n_min=25):
+    """(N_half, alpha, K) of the ASSA grid (ora_assa_params)."""
+    nh, a, K = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _load().ora_assa_params(float(sigma), float(v), float(fs), int(n_min), ctypes.byref(nh), ctypes.byref(a),
+                            ctypes.byref(K))
+    return nh.value, a.value, K.value
+
+
+def assa_forward(g: Gaussians, sigma, sensors, v, fs, t0, Nt, n_min=25, tau=0.0, want_amb=False):
+    """ASSA forward (Algorithm 1, ForwardOp) for Gaussians sharing the width sigma.
+    Returns y (Nd, Nt), or (y, amb) when want_amb."""
+    lib = _load()
+    s = _d(sensors).reshape(-1, 3)
+    Nd = s.shape[0]
+    cx, cy, cz = (_d(g.c[:, q]) for q in range(3))
+    y = np.zeros((Nd, Nt))
+    amb = np.zeros((Nd, Nt)) if want_amb else None
+    lib.ora_assa_forward(g.M, _p(cx), _p(cy), _p(cz), _p(_d(g.A)), float(sigma), Nd, _p(s), float(v), float(fs),
+                         float(t0), int(Nt), int(n_min), float(tau), _p(y), _p(amb))
+    return (y, amb) if want_amb else y
+
+
+def assa_adjoint(g: Gaussians, sigma, sensors, v, fs, t0, Nt, delta, n_min=25, tau=0.0, want_amb=False):
+    """ASSA adjoint (Algorithm 1, AdjointOp): g (M,), or (g, amb) when want_amb."""
+    lib = _load()
+    s = _d(sensors).reshape(-1, 3)
+    Nd = s.shape[0]
+    cx, cy, cz = (_d(g.c[:, q]) for q in range(3))
+    dl = _d(delta).reshape(Nd, Nt)
+    gA = np.zeros(g.M)
+    amb = np.zeros(g.M) if want_amb else None
+    lib.ora_assa_adjoint(g.M, _p(cx), _p(cy), _p(cz), float(sigma), Nd, _p(s), float(v), float(fs), float(t0),
+                         int(Nt), int(n_min), _p(dl), float(tau), _p(gA), _p(amb))
+    return (gA, amb) if want_amb else gA
 
 
 def voxelize(g: Gaussians, k, nx, ny, nz, ox, oy, oz, h):

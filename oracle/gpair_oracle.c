@@ -23,6 +23,9 @@
  *   ora_voxelize             pinned: separable numpy convolution (grid case), brute force.
  *   ora_adam_cawr / ora_ir   pinned: torch.optim.Adam + CosineAnnealingWarmRestarts on a dense
  *                                    operator built column by column from ora_forward.
+ *   ora_assa_forward/adjoint pinned: adjoint identity; the folded single-sum form; equality with
+ *                                    the windowed forward where every time of flight lies on the
+ *                                    upsampled grid; convergence to it as N_min grows.
  */
 #include <math.h>
 #include <stdint.h>
@@ -224,6 +227,156 @@ void ora_voxelize(int64_t M, const double* cx, const double* cy, const double* c
             }
         }
     }
+}
+
+/* ---------------------------------------------------------------------------------------
+ * ASSA: the paper's discretised operator (Methods, adaptive supersampling alignment;
+ * Algorithm 1), for Gaussians sharing one width sigma.
+ *
+ * Grid parameters (Methods, adaptive grid parameters): the kernel half-width in original samples
+ * N_half = ceil(3 sigma / (v dt)), dt = 1 / fs; the upsampling ratio
+ * alpha = max(1, ceil(((N_min - 1) / 2) / N_half)); the upsampled kernel half-width K = alpha N_half.
+ * Evaluated in double from the arguments as given. */
+void ora_assa_params(double sigma, double v, double fs, int n_min, int* n_half, int* alpha, int* K) {
+    int nh = (int)ceil(3.0 * sigma / (v / fs));
+    if (nh < 1) nh = 1;
+    int a = (int)ceil(((double)(n_min - 1) / 2.0) / (double)nh);
+    if (a < 1) a = 1;
+    *n_half = nh;
+    *alpha = a;
+    *K = a * nh;
+}
+
+/* The kernel h[k], k = -K..K, stored at h[k + K]: C d exp(-d^2 / 2 sigma^2) with
+ * d = -v k dt_up and C = 1/2 (the 1/(2r) factor of Eq. single_forward, split as 1/r in the
+ * projection times C in the kernel). */
+static void assa_kernel(double sigma, double v, double fs_up, int K, double* h) {
+    for (int k = -K; k <= K; ++k) {
+        double d = -v * (double)k / fs_up;
+        h[k + K] = 0.5 * d * exp(-d * d / (2.0 * sigma * sigma));
+    }
+}
+
+/* Snapped index of a pair on the upsampled grid (sample 0 at t0):
+ * k = floor((r / v - t0) fs_up + 1/2).  *tie is set when the rounding is within tau (in
+ * upsampled samples) of the other choice; *k_alt is that other choice. */
+static long assa_snap(double r, double v, double t0, double fs_up, double tau, int* tie, long* k_alt) {
+    double u = (r / v - t0) * fs_up + 0.5;
+    double f = floor(u);
+    long k = (long)f;
+    *tie = 0;
+    *k_alt = k;
+    if (u - f < tau) { *tie = 1; *k_alt = k - 1; }
+    else if (f + 1.0 - u < tau) { *tie = 1; *k_alt = k + 1; }
+    return k;
+}
+
+/* Forward, the paper's three stages per detector j:
+ *   1. projection:   z_j[k] = sum_i (x_i / r_ij) [k == k_ij],  k = 0..alpha Nt - 1
+ *   2. transposed convolution:  zt_j[k] = sum_m z_j[m] h[k - m]
+ *   3. decimation:   y_j[n] = zt_j[alpha n].
+ * Impulses snapped outside 0..alpha Nt - 1 are not in z (the sequence has that length).
+ * amb (optional): for pairs whose snap is within tau of a tie, |x_i / r_ij| times the change of
+ * their decimated contribution under the other choice, per sample. */
+void ora_assa_forward(int64_t M, const double* cx, const double* cy, const double* cz, const double* A,
+                      double sigma, int Nd, const double* sxyz, double v, double fs, double t0, int Nt,
+                      int n_min, double tau, double* y, double* amb) {
+    int nh, alpha, K;
+    ora_assa_params(sigma, v, fs, n_min, &nh, &alpha, &K);
+    const double fs_up = alpha * fs;
+    const long Nup = (long)alpha * Nt;
+    double* h = (double*)malloc(sizeof(double) * (size_t)(2 * K + 1));
+    assa_kernel(sigma, v, fs_up, K, h);
+    memset(y, 0, sizeof(double) * (size_t)Nd * (size_t)Nt);
+    if (amb) memset(amb, 0, sizeof(double) * (size_t)Nd * (size_t)Nt);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < Nd; ++j) {
+        double* z = (double*)calloc((size_t)Nup, sizeof(double));
+        double* zt = (double*)calloc((size_t)Nup, sizeof(double));
+        double sx = sxyz[3 * j], sy = sxyz[3 * j + 1], sz = sxyz[3 * j + 2];
+        double* yj = y + (size_t)j * Nt;
+        double* aj = amb ? amb + (size_t)j * Nt : NULL;
+        for (int64_t i = 0; i < M; ++i) {
+            if (A[i] == 0.0) continue;
+            double dx = cx[i] - sx, dy = cy[i] - sy, dz = cz[i] - sz;
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            int tie;
+            long k_alt;
+            long k = assa_snap(r, v, t0, fs_up, tau, &tie, &k_alt);
+            if (k >= 0 && k < Nup) z[k] += A[i] / r;
+            if (aj && tie) {
+                /* the pair's decimated contribution under either choice (zero when outside) */
+                for (long n = 0; n < Nt; ++n) {
+                    long q1 = alpha * n - k, q2 = alpha * n - k_alt;
+                    double c1 = (k >= 0 && k < Nup && q1 >= -K && q1 <= K) ? h[q1 + K] : 0.0;
+                    double c2 = (k_alt >= 0 && k_alt < Nup && q2 >= -K && q2 <= K) ? h[q2 + K] : 0.0;
+                    aj[n] += fabs(A[i] / r) * fabs(c1 - c2);
+                }
+            }
+        }
+        for (long k = 0; k < Nup; ++k) {
+            double acc = 0.0;
+            for (long m = k - K; m <= k + K; ++m)
+                if (m >= 0 && m < Nup) acc += z[m] * h[k - m + K];
+            zt[k] = acc;
+        }
+        for (int n = 0; n < Nt; ++n) yj[n] = zt[(long)alpha * n];
+        free(z);
+        free(zt);
+    }
+    free(h);
+}
+
+/* Adjoint, the transpose of each stage:
+ *   1. zero filling: dup_j[k] = delta_j[k / alpha] when alpha divides k, else 0
+ *   2. correlation with the flipped kernel: dconv_j[k] = sum_m h[m - k] dup_j[m]
+ *   3. back-projection: g_i = sum_j dconv_j[k_ij] / r_ij  (pairs snapped inside the sequence).
+ * amb (optional): per Gaussian, |dconv_j[k] - dconv_j[k_alt]| / r over pairs within tau of a tie. */
+void ora_assa_adjoint(int64_t M, const double* cx, const double* cy, const double* cz, double sigma,
+                      int Nd, const double* sxyz, double v, double fs, double t0, int Nt, int n_min,
+                      const double* delta, double tau, double* g, double* amb) {
+    int nh, alpha, K;
+    ora_assa_params(sigma, v, fs, n_min, &nh, &alpha, &K);
+    const double fs_up = alpha * fs;
+    const long Nup = (long)alpha * Nt;
+    double* h = (double*)malloc(sizeof(double) * (size_t)(2 * K + 1));
+    assa_kernel(sigma, v, fs_up, K, h);
+    double* dconv = (double*)malloc(sizeof(double) * (size_t)Nd * (size_t)Nup);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < Nd; ++j) {
+        double* dup = (double*)calloc((size_t)Nup, sizeof(double));
+        for (int n = 0; n < Nt; ++n) dup[(long)alpha * n] = delta[(size_t)j * Nt + n];
+        double* dc = dconv + (size_t)j * Nup;
+        for (long k = 0; k < Nup; ++k) {
+            double acc = 0.0;
+            for (long m = k - K; m <= k + K; ++m)
+                if (m >= 0 && m < Nup) acc += h[m - k + K] * dup[m];
+            dc[k] = acc;
+        }
+        free(dup);
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < M; ++i) {
+        double acc = 0.0, ab = 0.0;
+        for (int j = 0; j < Nd; ++j) {
+            double dx = cx[i] - sxyz[3 * j], dy = cy[i] - sxyz[3 * j + 1], dz = cz[i] - sxyz[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            int tie;
+            long k_alt;
+            long k = assa_snap(r, v, t0, fs_up, tau, &tie, &k_alt);
+            const double* dc = dconv + (size_t)j * Nup;
+            double c1 = (k >= 0 && k < Nup) ? dc[k] : 0.0;
+            acc += c1 / r;
+            if (tie) {
+                double c2 = (k_alt >= 0 && k_alt < Nup) ? dc[k_alt] : 0.0;
+                ab += fabs(c1 - c2) / r;
+            }
+        }
+        g[i] = acc;
+        if (amb) amb[i] = ab;
+    }
+    free(dconv);
+    free(h);
 }
 
 /* Cosine annealing with warm restarts (Methods, learning-rate schedule; SGDR semantics):

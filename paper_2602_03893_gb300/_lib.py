@@ -27,7 +27,7 @@ EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_vox
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
-           "gpair_wait_selftest", "gpair_version")
+           "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_version")
 
 
 class GpairError(RuntimeError):
@@ -87,6 +87,8 @@ def load(path: str | None = None):
         lib.gpair_release_scratch.argtypes = []
         lib.gpair_release_scratch.restype = None
         lib.gpair_wait_selftest.argtypes = [c_int, P]
+        lib.gpair_assa_forward.argtypes = [P, P, c_int, P, P]
+        lib.gpair_assa_adjoint.argtypes = [P, P, c_int, P, P, P]
         lib.gpair_version.restype = ctypes.c_char_p
         _lib = lib
     return _lib
@@ -218,6 +220,27 @@ def gpair_adjoint(g: Gaussians, arr: SensorArray, delta: torch.Tensor, gA: torch
     _check("gpair_adjoint", lib.gpair_adjoint(ctypes.byref(gc_), ctypes.byref(ac), _ptr(delta), _ptr(gA), _ptr(gc),
                                               _ptr(gsigma), _stream(stream)))
     return gA, gc, gsigma
+
+
+def gpair_assa_forward(g: Gaussians, arr: SensorArray, y: torch.Tensor, n_min: int = 25, stream=None) -> torch.Tensor:
+    """The paper's discretised forward operator (adaptive supersampling alignment), grid Gaussians."""
+    lib = load()
+    gc_, keep = g._c()
+    ac = arr._c()
+    _check("gpair_assa_forward", lib.gpair_assa_forward(ctypes.byref(gc_), ctypes.byref(ac), int(n_min), _ptr(y),
+                                                        _stream(stream)))
+    return y
+
+
+def gpair_assa_adjoint(g: Gaussians, arr: SensorArray, delta: torch.Tensor, gA: torch.Tensor, n_min: int = 25,
+                       stream=None) -> torch.Tensor:
+    """Transpose of gpair_assa_forward (amplitude gradient)."""
+    lib = load()
+    gc_, keep = g._c()
+    ac = arr._c()
+    _check("gpair_assa_adjoint", lib.gpair_assa_adjoint(ctypes.byref(gc_), ctypes.byref(ac), int(n_min), _ptr(delta),
+                                                        _ptr(gA), _stream(stream)))
+    return gA
 
 
 def gpair_voxelize(g: Gaussians, out_grid: Grid, window_k: float, vol: torch.Tensor, stream=None) -> torch.Tensor:

@@ -14,15 +14,6 @@ namespace gp {
 constexpr int ADJ_THREADS = TILE;
 constexpr int ADJ_SC = 32;   // sensors staged per chunk
 
-struct KahanF {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        float y = x - c;
-        float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
 
 
 // Window sums of one pair: s1 = sum dl d e (amplitude gradient); with FULL also s0 = sum dl e,

@@ -1,0 +1,317 @@
+// assa.cu -- the paper's discretised operator (Methods, adaptive supersampling alignment;
+// Algorithm 1) for grid Gaussians sharing one width.  Each pair's time of flight is snapped to
+// the nearest sample of a grid alpha times finer than fs, the pair's mass A / r accumulates at
+// that sample, the impulse lines are convolved with the sampled pulse h and decimated back to
+// fs.  The adjoint transposes each stage: zero filling, correlation with h, back-projection.
+//
+// Forward decomposition: as the exact forward (forward.cu), CTA = (slab of bricks, 8 sensors),
+// one warp per sensor, bricks streamed through a ring of TMA-filled shared buffers.  Each warp
+// keeps its sensor's impulse line over the slab's band on the fine grid in shared memory and
+// adds every pair's mass there with a shared-memory atomic; after the slab it convolves and
+// decimates the band into the slab's partial row (summed over slabs by slab_reduce_kernel).
+// Adjoint: the correlated residual dconv_j[k] = sum_n h[alpha n - k] delta_j[n] is formed once
+// per sensor (assa_dconv_kernel); then one thread per Gaussian gathers dconv at its snapped
+// samples over all sensors, Kahan-compensated, and writes its gradient once.
+#include <cuda.h>
+
+#include <cstring>
+
+#include "gpair_internal.cuh"
+
+namespace gp {
+
+constexpr int ASSA_SPC = 8;
+constexpr int ASSA_THREADS = 32 * ASSA_SPC;
+constexpr int ASSA_RING = 4;
+constexpr int ASSA_ADJ_SC = 32;
+
+struct AssaSmem {
+    float tileA[ASSA_RING][TILE];
+    uint64_t full[ASSA_RING];
+    int released[ASSA_RING];
+    int issued[ASSA_RING];
+    int abort;
+};
+constexpr size_t ASSA_HDR = (sizeof(AssaSmem) + 127) & ~(size_t)127;
+
+// Impulse band of one (slab, sensor) on the fine grid: samples alpha w - K .. alpha (w + LB - 1) + K.
+__host__ __device__ __forceinline__ int assa_zb(int LB, int alpha, int K) { return (alpha * LB + 2 * K + 3) & ~3; }
+
+// alpha n0, clamped far outside any record (the snapped sample then fails the range tests).
+__device__ __forceinline__ int assa_an0(int alpha, int n0) {
+    const long long an = (long long)alpha * n0;
+    return (int)max(min(an, (long long)(1 << 30)), -(long long)(1 << 30));
+}
+
+__global__ void __launch_bounds__(ASSA_THREADS)
+assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
+                int2* __restrict__ rows, int LB, int* status, int use_tma, const __grid_constant__ CUtensorMap tmap,
+                const __grid_constant__ AssaTable T) {
+    static_assert(BX == 8 && BY == 8 && BZ == 4 && TILE == 256,
+                  "lane offsets below assume lane + 32 q -> (lane & 7, (lane >> 3) + 4 (q & 1), q >> 1)");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    AssaSmem& S = *reinterpret_cast<AssaSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int alpha = T.alpha, K = T.K;
+    const int ZB = assa_zb(LB, alpha, K);
+    float* zb = reinterpret_cast<float*>(smem_raw + ASSA_HDR) + (size_t)warp * ZB;
+
+    const int slab = blockIdx.y;
+    const int j = blockIdx.x * ASSA_SPC + warp;
+    const bool has_sensor = j < a.Nd;
+    const SlabInfo sl = slabs[slab];
+    const int nTiles = sl.t_end - sl.t_begin;
+    const size_t row = (size_t)slab * a.Nd + (has_sensor ? j : 0);
+    float* prow = partial + row * LB;
+    const int Nup = alpha * a.Nt;
+
+    // the slab's sample band for this sensor; a.k * sigma covers the pulse half-width plus half
+    // a fine step of snapping
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    int n_lo = 0, n_hi = -1;
+    if (has_sensor) {
+        sx = a.xyz[3 * j]; sy = a.xyz[3 * j + 1]; sz = a.xyz[3 * j + 2];
+        if (nTiles > 0) {
+            double dmin, dmax;
+            box_distance(sl, sx, sy, sz, dmin, dmax);
+            double ks = (double)a.k * sl.smax;
+            double lo = floor(((dmin - ks) / a.v - a.t0) * a.fs) - 2.0;
+            double hi = ceil(((dmax + ks) / a.v - a.t0) * a.fs) + 2.0;
+            if (lo < 0) lo = 0;
+            if (hi > a.Nt - 1) hi = a.Nt - 1;
+            if (lo <= hi) { n_lo = (int)lo; n_hi = (int)hi; }
+        }
+    }
+    const int w = n_lo & ~3;
+    bool active = has_sensor && n_lo <= n_hi;
+    if (active && n_hi + 1 - w > LB) {     // cannot happen with the host's band bound
+        set_status(status, DEV_CAPACITY);
+        n_hi = w + LB - 1;
+    }
+    if (lane == 0 && has_sensor) rows[row] = make_int2(w, active ? min(LB, a.Nt - w) : 0);
+    if (threadIdx.x == 0) {
+        S.abort = 0;
+        for (int b = 0; b < ASSA_RING; ++b) {
+            S.released[b] = 0;
+            S.issued[b] = -1;
+            mbar_init(&S.full[b], 1);
+        }
+        fence_mbar_init();
+    }
+    for (int q = lane; q < ZB; q += 32) zb[q] = 0.f;
+    __syncthreads();
+
+    const bool tma = use_tma != 0;
+    auto fill = [&](int TT) {
+        const int b = TT % ASSA_RING;
+        int tx, ty, tz;
+        slab_brick(sl, TT, tx, ty, tz);
+        if (tma) {
+            if (lane == 0) {
+                S.issued[b] = TT;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect_tx(&S.full[b], TILE * sizeof(float));
+                tma_load_3d(&S.tileA[b][0], &tmap, tx * BX, ty * BY, tz * BZ, &S.full[b]);
+            }
+        } else {
+            for (int q = lane; q < TILE; q += 32) {
+                const int gx = tx * BX + (q & (BX - 1)), gy = ty * BY + ((q / BX) & (BY - 1)), gz = tz * BZ + q / (BX * BY);
+                const bool ok = gx < g.nx && gy < g.ny && gz < g.nz;
+                S.tileA[b][q] = ok ? g.A[((int64_t)gz * g.ny + gy) * g.nx + gx] : 0.f;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.full[b]);
+        }
+    };
+    if (warp == 0)
+        for (int TT = 0; TT < ASSA_RING && TT < nTiles; ++TT) fill(TT);
+
+    const float aInvD = (float)alpha * a.invDelta;     // fine samples per metre
+    const int kb0 = alpha * w - K;                     // fine sample at zb[0]
+    const float h = g.h;
+    const float ox = ((float)(lane & 7) - 0.5f * (BX - 1)) * h;
+    const float oy0 = ((float)(lane >> 3) - 0.5f * (BY - 1)) * h;
+    const float oy1 = ((float)((lane >> 3) + 4) - 0.5f * (BY - 1)) * h;
+
+    PairRef refs;
+    int t = 0;
+    bool ok = true;
+    for (; t < nTiles; ++t) {
+        const int b = t % ASSA_RING;
+        if (!mbar_wait(&S.full[b], (uint32_t)((t / ASSA_RING) & 1))) {
+            ok = false;
+            break;
+        }
+        if (active) {
+            if ((t & 31) == 0 && t + lane < nTiles) {
+                int tx, ty, tz;
+                slab_brick(sl, t + lane, tx, ty, tz);
+                refs = make_ref(g.ox + (tx * BX + BX / 2) * (double)g.h, g.oy + (ty * BY + BY / 2) * (double)g.h,
+                                g.oz + (tz * BZ + BZ / 2) * (double)g.h, sx, sy, sz, a);
+            }
+            const int src = t & 31;
+            PairRef r;
+            r.v0x = __shfl_sync(0xffffffffu, refs.v0x, src);
+            r.v0y = __shfl_sync(0xffffffffu, refs.v0y, src);
+            r.v0z = __shfl_sync(0xffffffffu, refs.v0z, src);
+            r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
+            r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
+            r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
+            const int an0 = assa_an0(alpha, r.n0);
+            const float ax = ox * (2.f * r.v0x + ox);
+            const float ay0 = oy0 * (2.f * r.v0y + oy0), ay1 = oy1 * (2.f * r.v0y + oy1);
+#pragma unroll
+            for (int q = 0; q < TILE / 32; ++q) {
+                const float Ai = S.tileA[b][lane + 32 * q];
+                const float oz = ((float)(q >> 1) - 0.5f * (BZ - 1)) * h;
+                const float num = (ax + ((q & 1) ? ay1 : ay0)) + oz * (2.f * r.v0z + oz);
+                float invR, phi;
+                pair_phase_num(r, num, invR, phi);
+                // snapped fine sample: floor((R / v - t0) alpha fs + 1/2) = alpha n0 + floor(phi alpha / Delta + 1/2)
+                const int k = an0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
+                const int kb = k - kb0;
+                if (Ai != 0.f && k >= 0 && k < Nup && kb >= 0 && kb < ZB) atomicAdd(&zb[kb], Ai * invR);
+            }
+        }
+        // release the slot; the warp that releases it last refills it with tile t + ASSA_RING
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = (atomicAdd(&S.released[b], 1) + 1) % ASSA_SPC == 0;
+            if (last) __threadfence_block();
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last && t + ASSA_RING < nTiles) fill(t + ASSA_RING);
+    }
+    if (!ok && lane == 0) {
+        set_status(status, DEV_TIMEOUT);
+        S.abort = 1;
+    }
+    __syncthreads();
+    if (S.abort) {
+        if (tma && threadIdx.x == 0)
+            for (int b = 0; b < ASSA_RING; ++b)
+                if (S.issued[b] >= 0) mbar_wait(&S.full[b], (uint32_t)((S.issued[b] / ASSA_RING) & 1));
+        return;
+    }
+    if (active) {
+        // y[n] = sum_m z[m] h[alpha n - m]; sample n = w + q needs zb[alpha q .. alpha q + 2K]
+        const int wend = min(a.Nt, w + LB);
+        for (int q = lane; q < wend - w; q += 32) {
+            const float* zq = zb + (size_t)alpha * q;
+            float y = 0.f;
+            for (int tt = 0; tt <= 2 * K; ++tt) y = fmaf(zq[tt], T.hr[tt], y);   // h[alpha n - m] = h[K - tt]
+            prow[q] = y;
+        }
+    }
+}
+
+// dconv_j[k] = sum_n h[alpha n - k] delta_j[n], k = 0 .. alpha Nt - 1 (zero filling and the
+// correlation with the flipped pulse in one pass).  Block: 256 fine samples of one sensor.
+__device__ __forceinline__ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+__global__ void assa_dconv_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ AssaTable T,
+                                  float* __restrict__ dconv) {
+    extern __shared__ float sd[];
+    const int j = blockIdx.y;
+    const int alpha = T.alpha, K = T.K;
+    const int Nup = alpha * Nt;
+    const int k0 = blockIdx.x * 256;
+    const int na = -floor_div(-(k0 - K), alpha);            // ceil((k0 - K) / alpha)
+    const int nb = floor_div(k0 + 255 + K, alpha);
+    const float* dj = delta + (size_t)j * Nt;
+    for (int q = threadIdx.x; q <= nb - na; q += blockDim.x) {
+        const int n = na + q;
+        sd[q] = (n >= 0 && n < Nt) ? dj[n] : 0.f;
+    }
+    __syncthreads();
+    const int k = k0 + (int)threadIdx.x;
+    if (k >= Nup) return;
+    const int n1 = -floor_div(-(k - K), alpha), n2 = floor_div(k + K, alpha);
+    float acc = 0.f;
+    for (int n = n1; n <= n2; ++n) acc = fmaf(T.hr[K - (alpha * n - k)], sd[n - na], acc);
+    dconv[(size_t)j * Nup + k] = acc;
+}
+
+size_t assa_dconv_smem(const AssaTable& T) { return (size_t)((255 + 2 * T.K) / T.alpha + 3) * sizeof(float); }
+
+// g_i = sum_j dconv_j[k_ij] / r_ij.  One CTA per brick, one thread per Gaussian, all sensors in
+// chunks of 32 with FP64 references prepared one chunk ahead by the last warp.
+__global__ void __launch_bounds__(TILE)
+assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __grid_constant__ AssaTable T,
+                float* __restrict__ gA) {
+    __shared__ PairRef refs2[2][ASSA_ADJ_SC];
+    const int64_t t = blockIdx.x;
+    const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
+    const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
+    const int gx = tx * BX + (l & (BX - 1)), gy = ty * BY + ((l / BX) & (BY - 1)), gz = tz * BZ + l / (BX * BY);
+    const bool valid = gx < g.nx && gy < g.ny && gz < g.nz;
+    const int64_t i = ((int64_t)gz * g.ny + gy) * g.nx + gx;
+    float dx, dy, dz;
+    brick_offset(l, g.h, dx, dy, dz);
+    const double c0x = g.ox + (tx * BX + BX / 2) * (double)g.h;
+    const double c0y = g.oy + (ty * BY + BY / 2) * (double)g.h;
+    const double c0z = g.oz + (tz * BZ + BZ / 2) * (double)g.h;
+    const int alpha = T.alpha;
+    const int Nup = alpha * a.Nt;
+    const float aInvD = (float)alpha * a.invDelta;
+    constexpr int LASTW = TILE / 32 - 1;
+    KahanF kA;
+    if (warp == LASTW && lane < min(ASSA_ADJ_SC, a.Nd))
+        refs2[0][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * lane], a.xyz[3 * lane + 1], a.xyz[3 * lane + 2], a);
+    int cur = 0;
+    for (int j0 = 0; j0 < a.Nd; j0 += ASSA_ADJ_SC, cur ^= 1) {
+        const int nsc = min(ASSA_ADJ_SC, a.Nd - j0);
+        __syncthreads();
+        if (warp == LASTW && j0 + ASSA_ADJ_SC + lane < a.Nd) {
+            const int j = j0 + ASSA_ADJ_SC + lane;
+            refs2[cur ^ 1][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        }
+        const PairRef* refs = refs2[cur];
+        if (valid) {
+#pragma unroll 4
+            for (int q = 0; q < nsc; ++q) {
+                const PairRef r = refs[q];
+                float invR, phi;
+                pair_phase_fast(r, dx, dy, dz, invR, phi);
+                const int k = assa_an0(alpha, r.n0) + (int)floorf(fmaf(phi, aInvD, 0.5f));
+                if (k >= 0 && k < Nup) kA.add(__ldg(dconv + (size_t)(j0 + q) * Nup + k) * invR);
+            }
+        }
+    }
+    if (valid) gA[i] = kA.s;
+}
+
+// ---- host side -----------------------------------------------------------------------------
+
+size_t assa_fwd_smem(int LB, const AssaTable& T) {
+    return ASSA_HDR + (size_t)ASSA_SPC * assa_zb(LB, T.alpha, T.K) * sizeof(float);
+}
+
+cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
+                                int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
+                                cudaStream_t st) {
+    static const CUtensorMap zero_map = [] { CUtensorMap z; memset(&z, 0, sizeof(z)); return z; }();
+    const size_t smem = assa_fwd_smem(LB, T);
+    cudaError_t e = cudaFuncSetAttribute(assa_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.Nd + ASSA_SPC - 1) / ASSA_SPC, S);
+    assa_fwd_kernel<<<grid, ASSA_THREADS, smem, st>>>(g, a, si, partial, rows, LB, status, tmap != nullptr,
+                                                      tmap ? *tmap : zero_map, T);
+    return cudaGetLastError();
+}
+
+size_t assa_dconv_bytes(const ArrDev& a, const AssaTable& T) { return (size_t)a.Nd * T.alpha * a.Nt * sizeof(float); }
+
+cudaError_t launch_assa_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, const AssaTable& T,
+                                float* dconv, cudaStream_t st) {
+    dim3 dgrid((T.alpha * a.Nt + 255) / 256, a.Nd);
+    assa_dconv_kernel<<<dgrid, 256, assa_dconv_smem(T), st>>>(delta, a.Nt, T, dconv);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    assa_adj_kernel<<<(unsigned)g.ntiles, TILE, 0, st>>>(g, a, dconv, T, gA);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -158,27 +158,7 @@ struct FwdSmem {
 // then per warp an FP64 slab band of LB entries.
 constexpr size_t FWD_HDR = (sizeof(FwdSmem) + 127) & ~(size_t)127;
 
-__device__ __forceinline__ void box_distance(const SlabInfo& sl, float sx, float sy, float sz,
-                                             double& dmin, double& dmax) {
-    double s[3] = {sx, sy, sz}, mn = 0, mx = 0;
-    for (int q = 0; q < 3; ++q) {
-        double lo = sl.lo[q], hi = sl.hi[q];
-        double a = lo - s[q], b = s[q] - hi;
-        double out = a > 0 ? a : (b > 0 ? b : 0.0);
-        mn += out * out;
-        double far = fabs(s[q] - lo) > fabs(s[q] - hi) ? fabs(s[q] - lo) : fabs(s[q] - hi);
-        mx += far * far;
-    }
-    dmin = sqrt(mn);
-    dmax = sqrt(mx);
-}
 
-// Tile t (0-based within the slab) -> brick coordinates (grid mode).
-__device__ __forceinline__ void slab_brick(const SlabInfo& sl, int t, int& tx, int& ty, int& tz) {
-    tx = sl.bx0 + t % sl.bdx;
-    ty = sl.by0 + (t / sl.bdx) % sl.bdy;
-    tz = sl.bz0 + t / (sl.bdx * sl.bdy);
-}
 
 // banded = 1 (grid mode): the partial row of (slab, sensor) holds only the slab's band window,
 // at offset rows[].x, length rows[].y; PL = LB.  banded = 0: full rows of PL = N_t samples,

@@ -29,6 +29,12 @@ cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const floa
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
 cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t st);
+cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
+                                int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
+                                cudaStream_t st);
+size_t assa_dconv_bytes(const ArrDev& a, const AssaTable& T);
+cudaError_t launch_assa_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, const AssaTable& T,
+                                float* dconv, cudaStream_t st);
 cudaError_t launch_resid(const float* y, const float* b, float* delta, float scale, int64_t n, double* partial,
                          double* out, cudaStream_t st);
 cudaError_t launch_reduce2(const float* a, const float* b, const float* c, int64_t n, double* partial, double* out,
@@ -504,6 +510,83 @@ gpair_status gpair_last_device_status(void* stream) {
     if (h == DEV_TIMEOUT) return GPAIR_ERR_TIMEOUT;
     if (h == DEV_CAPACITY) return GPAIR_ERR_UNSUPPORTED;
     return GPAIR_OK;
+}
+
+// ---- the paper's operator (Methods, adaptive supersampling alignment; Algorithm 1) -------------
+
+// Grid parameters and the sampled pulse: N_half = ceil(3 sigma / (v / fs)),
+// alpha = max(1, ceil(((N_min - 1) / 2) / N_half)), K = alpha N_half, all in double from the
+// arguments as given; hr[t] = h[K - t], h[k] = (1/2) d exp(-d^2 / 2 sigma^2), d = -v k / (alpha fs).
+bool make_assa_table(const GaussDev& g, const ArrDev& a, int n_min, AssaTable& T) {
+    const double s = g.sigma, v = a.v, fs = a.fs;
+    int nh = (int)std::ceil(3.0 * s / (v / fs));
+    if (nh < 1) nh = 1;
+    int alpha = (int)std::ceil(((double)(n_min - 1) / 2.0) / (double)nh);
+    if (alpha < 1) alpha = 1;
+    if ((int64_t)alpha * nh > ASSA_KMAX || (int64_t)alpha * a.Nt >= (1LL << 30)) return false;
+    T.alpha = alpha;
+    T.n_half = nh;
+    T.K = alpha * nh;
+    const double fs_up = alpha * fs;
+    for (int t = 0; t <= 2 * ASSA_KMAX; ++t) T.hr[t] = 0.f;
+    for (int t = 0; t <= 2 * T.K; ++t) {
+        const double d = -v * (double)(T.K - t) / fs_up;
+        T.hr[t] = (float)(0.5 * d * std::exp(-d * d / (2.0 * s * s)));
+    }
+    return true;
+}
+
+gpair_status assa_inputs(const gpair_gaussians* gi, const gpair_array* ai, int n_min, GaussDev& g, ArrDev& a,
+                         AssaTable& T) {
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (n_min < 1) return GPAIR_ERR_INVALID_ARG;
+    if (!g.grid) return GPAIR_ERR_UNSUPPORTED;      // one pulse table: a shared width
+    if (!make_assa_table(g, a, n_min, T)) return GPAIR_ERR_UNSUPPORTED;
+    return GPAIR_OK;
+}
+
+gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai, int n_min, float* y, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    AssaTable T;
+    gpair_status s = assa_inputs(gi, ai, n_min, g, a, T);
+    if (s != GPAIR_OK) return s;
+    if (!y) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the slab bands must hold the pulse half-width N_half v / fs plus half a fine step of snapping
+    ArrDev aa = a;
+    aa.k = (float)((T.n_half * (double)a.Delta + 0.5 * (double)a.Delta / T.alpha) / (double)g.sigma * 1.001 + 1e-3);
+    FwdPlan p = plan_forward(g, aa);
+    void* scratch = nullptr;
+    int* status = nullptr;
+    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    char* base = static_cast<char*>(scratch);
+    SlabInfo* si = reinterpret_cast<SlabInfo*>(base + p.off_si);
+    int2* rows = reinterpret_cast<int2*>(base + p.off_rows);
+    float* part = reinterpret_cast<float*>(base + p.off_part);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    const bool tma = make_tmap(g, &map);
+    cudaError_t e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
+    if (e == cudaSuccess) e = launch_assa_forward(g, aa, si, p.S, part, rows, p.LB, status, tma ? &map : nullptr, T, st);
+    if (e == cudaSuccess) e = launch_slab_reduce(g, aa, part, rows, p.S, p.PL, y, st);
+    return cuda_status(e);
+}
+
+gpair_status gpair_assa_adjoint(const gpair_gaussians* gi, const gpair_array* ai, int n_min, const float* delta,
+                                float* gA, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    AssaTable T;
+    gpair_status s = assa_inputs(gi, ai, n_min, g, a, T);
+    if (s != GPAIR_OK) return s;
+    if (!delta || !gA) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    if ((s = get_scratch(st, assa_dconv_bytes(a, T), &scratch, nullptr)) != GPAIR_OK) return s;
+    return cuda_status(launch_assa_adjoint(g, a, delta, gA, T, static_cast<float*>(scratch), st));
 }
 
 gpair_status gpair_wait_selftest(int polls, void* stream) {

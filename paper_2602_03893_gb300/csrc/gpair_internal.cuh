@@ -110,6 +110,15 @@ __device__ __forceinline__ float edge_sign(const MomentTable& T, float dE, float
     return inside == (T.edge_in != 0) ? 0.f : (inside ? 1.f : -1.f);
 }
 
+// The paper's discretised operator (Methods, adaptive supersampling alignment): pulse centres
+// snapped to a grid ALPHA times finer than fs, pulse sampled there over |k| <= K.
+// hr[t] = h[K - t], t = 0..2K, with h[k] = (1/2) d exp(-d^2 / 2 sigma^2), d = -v k / (alpha fs).
+constexpr int ASSA_KMAX = 256;
+struct AssaTable {
+    int alpha, K, n_half;
+    float hr[2 * ASSA_KMAX + 1];
+};
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -185,6 +194,40 @@ __device__ __forceinline__ void pair_phase_fast(const PairRef& r, float dx, floa
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(r.R0 + R));
     phi = fmaf(num, rc, r.phi0);
 }
+
+// Nearest and farthest distance from a sensor to a slab's box of Gaussian centres (FP64).
+__device__ __forceinline__ void box_distance(const SlabInfo& sl, float sx, float sy, float sz,
+                                             double& dmin, double& dmax) {
+    double s[3] = {sx, sy, sz}, mn = 0, mx = 0;
+    for (int q = 0; q < 3; ++q) {
+        double lo = sl.lo[q], hi = sl.hi[q];
+        double a = lo - s[q], b = s[q] - hi;
+        double out = a > 0 ? a : (b > 0 ? b : 0.0);
+        mn += out * out;
+        double far = fabs(s[q] - lo) > fabs(s[q] - hi) ? fabs(s[q] - lo) : fabs(s[q] - hi);
+        mx += far * far;
+    }
+    dmin = sqrt(mn);
+    dmax = sqrt(mx);
+}
+
+// Tile t (0-based within the slab) -> brick coordinates (grid mode).
+__device__ __forceinline__ void slab_brick(const SlabInfo& sl, int t, int& tx, int& ty, int& tz) {
+    tx = sl.bx0 + t % sl.bdx;
+    ty = sl.by0 + (t / sl.bdx) % sl.bdy;
+    tz = sl.bz0 + t / (sl.bdx * sl.bdy);
+}
+
+// Kahan-compensated FP32 sum.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
 
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicMax(status, code);

@@ -365,3 +365,86 @@ def test_ir_line_search_is_exact_minimiser():
     alpha = -x1[0] / g[0] if g[0] != 0 else -x1[1] / g[1]
     assert np.allclose(x1, -alpha * g, rtol=1e-10)
     assert f(alpha) <= f(alpha * 1.01) and f(alpha) <= f(alpha * 0.99)
+
+
+# ---------------------------------------------------------------- ASSA (Algorithm 1)
+
+def _assa_case(seed=21):
+    g = synth.centred_grid(6, 5, 4, 0.1e-3)
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0.2, 1.0, g.M)
+    G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, A)
+    sens = synth.cap_sensors(7, 6e-3, 150.0)
+    return g, G, sens, 1500.0, 40e6, 0.0, 512
+
+
+def test_assa_adjoint_identity():
+    g, G, sens, v, fs, t0, Nt = _assa_case()
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.0, 1.0, G.M)
+    delta = rng.normal(size=(len(sens), Nt))
+    Gx = oracle.Gaussians(G.c, G.sigma, x)
+    Fx = oracle.assa_forward(Gx, g.sigma, sens, v, fs, t0, Nt)
+    FTd = oracle.assa_adjoint(Gx, g.sigma, sens, v, fs, t0, Nt, delta)
+    lhs, rhs = float(np.sum(Fx * delta)), float(x @ FTd)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Fx) * np.linalg.norm(delta)
+
+
+def test_assa_stages_equal_the_folded_single_sum():
+    """Projection, transposed convolution and decimation collapse to
+    y_j[n] = sum_i (x_i / r_ij) h[alpha n - k_ij] over |alpha n - k_ij| <= K; evaluated here pair by
+    pair, which checks the staging's index conventions (kernel orientation, decimation phase)."""
+    g, G, sens, v, fs, t0, Nt = _assa_case()
+    nh, alpha, K = oracle.assa_params(g.sigma, v, fs)
+    fs_up = alpha * fs
+    y = oracle.assa_forward(G, g.sigma, sens, v, fs, t0, Nt)
+    yd = np.zeros_like(y)
+    n = np.arange(Nt)
+    for j, s in enumerate(sens):
+        r = np.linalg.norm(G.c - s, axis=1)
+        k = np.floor((r / v - t0) * fs_up + 0.5).astype(np.int64)
+        for i in range(G.M):
+            q = alpha * n - k[i]
+            m = np.abs(q) <= K
+            d = -v * q[m] / fs_up
+            yd[j, m] += G.A[i] / r[i] * 0.5 * d * np.exp(-d * d / (2 * g.sigma ** 2))
+    assert np.abs(y).max() > 0
+    assert np.linalg.norm(y - yd) <= 1e-12 * np.linalg.norm(yd)
+
+
+def test_assa_equals_windowed_forward_when_times_of_flight_are_on_the_grid():
+    """Gaussians on the axes through one sensor at distances v k / fs_up: snapping is exact, and
+    ASSA then equals the outgoing term of Eq. (single_forward) over the window
+    |d| <= N_half v / fs (K upsampled samples), as evaluated by the windowed forward."""
+    v, fs, t0, Nt, sigma = 1500.0, 40e6, 0.0, 2048, 0.1e-3
+    nh, alpha, K = oracle.assa_params(sigma, v, fs)
+    fs_up = alpha * fs
+    ks = [1500, 1623, 1777, 2101, 2400, 2999]
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [-1, 0, 0], [0, -1, 0], [0, 0, -1]], float)
+    c = np.array([v * k / fs_up * d for k, d in zip(ks, dirs)])
+    A = np.random.default_rng(2).uniform(0.5, 1.5, len(ks))
+    G = oracle.Gaussians(c, np.full(len(ks), sigma), A)
+    sens = np.zeros((1, 3))
+    y = oracle.assa_forward(G, sigma, sens, v, fs, t0, Nt)
+    # window just wider than N_half v dt by less than one upsampled step: the same sample set
+    kw = (nh + 0.4 / alpha) * (v / fs) / sigma
+    yw = oracle.forward(G, sens, v, fs, t0, Nt, k=kw)
+    assert np.abs(yw).max() > 0
+    assert np.linalg.norm(y - yw) <= 1e-12 * np.linalg.norm(yw)
+
+
+def test_assa_converges_to_the_windowed_forward_as_n_min_grows():
+    """The snapping error is at most half an upsampled step, so the difference to the exact
+    windowed operator falls roughly as 1 / alpha."""
+    g, G, sens, v, fs, t0, Nt = _assa_case(seed=4)
+    nh, _, _ = oracle.assa_params(g.sigma, v, fs)
+    kw = nh * (v / fs) / g.sigma             # ASSA's window, |d| <= N_half v dt, for every alpha
+    yw = oracle.forward(G, sens, v, fs, t0, Nt, k=kw)
+    errs = []
+    for n_min in (25, 101, 401):
+        _, alpha, _ = oracle.assa_params(g.sigma, v, fs, n_min)
+        y = oracle.assa_forward(G, g.sigma, sens, v, fs, t0, Nt, n_min=n_min)
+        errs.append((alpha, np.linalg.norm(y - yw) / np.linalg.norm(yw)))
+    (a1, e1), (a2, e2), (a3, e3) = errs
+    assert e2 < e1 * 2.0 * a1 / a2 and e3 < e2 * 2.0 * a2 / a3, errs
+    assert all(0.005 < e * a < 0.05 for a, e in errs), errs     # error x alpha roughly constant
