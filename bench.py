@@ -38,7 +38,8 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 MUFU_LANES_PER_SM = 32          # MUFU lanes per SM (ex2 measured at ~30 lane-ops / clk / SM)
-LAUNCHES_PER_STEP = 9           # npc, slab info, forward slab, slab reduce, resid, finish, tile info, adjoint, adam
+LAUNCHES_PER_STEP = 9           # npc, slab info, forward, slab reduce, resid, finish, Q table, adjoint, adam
+ASSA_NMIN = 25                  # the paper's minimum number of fine samples across the pulse
 
 
 def parse():
@@ -50,12 +51,17 @@ def parse():
     p.add_argument("--workload", default="paper", choices=["paper", "mid", "tiny"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sensors", type=int, default=32)
+    p.add_argument("--no-assa", action="store_true", help="skip timing the paper's ASSA operator")
     return p.parse_args()
 
 
 def workload(name):
     from paper_2602_03893_gb300 import synth
     return {"paper": synth.paper_scale, "mid": synth.mid, "tiny": synth.tiny}[name]()
+
+
+def pairs_of(w):
+    return float(w.M) * w.Nd
 
 
 def work_units(w):
@@ -336,6 +342,36 @@ def main():
     e2e = {"value": tw / (e2e_steps * world), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 4),
            "d2h_bytes_per_step": 8, "loss_last": loss}
 
+    # ---- the paper's own operator (ASSA, Algorithm 1) on the same workload and the solver's image,
+    # timed after the IR step; the paper's figures (RTX 5090) are context
+    assa = None
+    if not args.no_assa:
+        x_img = solver.gpair_solver_image()
+        gx = _lib.Gaussians(A=x_img, grid=grid)
+        ya, ga = torch.empty_like(b), torch.empty_like(x_img)
+        ra = torch.randn(b.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        times = {}
+        for name, fn in (("forward", lambda: _lib.gpair_assa_forward(gx, arr, ya, n_min=ASSA_NMIN)),
+                         ("adjoint", lambda: _lib.gpair_assa_adjoint(gx, arr, ra, ga, n_min=ASSA_NMIN))):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = max_over_ranks(a0.elapsed_time(a1) / args.steps, world)
+        assert _lib.gpair_last_device_status() == 0
+        nh = math.ceil(3.0 * float(np.float32(g.sigma)) / (float(np.float32(w.v)) / float(np.float32(w.fs))))
+        alpha = max(1, math.ceil(((ASSA_NMIN - 1) / 2.0) / nh))
+        assa = {"n_min": ASSA_NMIN, "alpha": alpha, "n_half": nh, "forward_ms": times["forward"],
+                "adjoint_ms": times["adjoint"], "fwd_plus_adj_ms": times["forward"] + times["adjoint"],
+                "pair_evals_per_s": 2 * pairs_of(w) / ((times["forward"] + times["adjoint"]) / 1e3),
+                "paper_ms": {"forward": 37.41, "adjoint": 4.99, "hardware": "RTX 5090 (the paper's)"},
+                "includes": "forward: slab info + kernel + slab reduction; adjoint: correlated residual + kernel"}
+
     clocks = sampler.summary()
     pairs, samples = work_units(w)
     fwd_avg = fwd_ms / max(nrec, 1) / 1e3
@@ -385,7 +421,7 @@ def main():
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
                               "step_device": step_ms / max(nrec, 1)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "assa": assa, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     solver.close()

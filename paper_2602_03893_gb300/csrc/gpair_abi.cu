@@ -140,6 +140,10 @@ gpair_status make_arr(const gpair_array* ai, ArrDev& a) {
     a.k = ai->window_k;
     a.Delta = (float)((double)ai->sound_speed / (double)ai->fs);
     a.invDelta = (float)((double)ai->fs / (double)ai->sound_speed);
+    a.fs_v = (double)ai->fs / (double)ai->sound_speed;
+    a.t0fs = (double)ai->t0 * (double)ai->fs;
+    a.vt0 = (double)ai->sound_speed * (double)ai->t0;
+    a.dlt = (double)ai->sound_speed / (double)ai->fs;
     return GPAIR_OK;
 }
 

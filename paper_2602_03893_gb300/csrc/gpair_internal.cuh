@@ -49,6 +49,8 @@ struct ArrDev {
     float k;
     float Delta;             // v / fs: metres per sample
     float invDelta;          // fs / v
+    double fs_v, t0fs;       // fs / v and t0 fs, for the reference sample n0
+    double vt0, dlt;         // v t0 and v / fs, for the reference phase
 };
 
 // Per-tile summary: reference point (float, so that FP64 differences with it are exact), the
@@ -129,16 +131,27 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // kernels (w - n0, Nt - 1 - n0, ...) stays inside int32.
 constexpr double N0_CLAMP = 268435456.0;   // 2^28
 
-// Reference for tile centre c0 and sensor s, in FP64.  t_n = t0 + n / fs exactly as the operator
-// defines it.
+// Reference for tile centre c0 and sensor s, in FP64 (GB300 runs FP64 at a small fraction of the
+// FP32 rate, so the reference avoids double division and square root).  R0 = |c0 - s| from one
+// Newton-Raphson step y1 = y0 (3 - q y0^2) / 2 for 1 / sqrt(q), started from the FP32 rsqrt
+// (relative error ~1e-7 -> ~1e-14); n0 is the nearest sample up to rounding (any nearby integer
+// serves: phi0 is formed from the same n0); phi0 = R0 - v (t0 + n0 / fs) with v t0 and v / fs
+// from the host (error ~1e-15 m).
 __device__ __forceinline__ PairRef make_ref(double c0x, double c0y, double c0z, float sx, float sy,
                                             float sz, const ArrDev& a) {
     double vx = c0x - (double)sx, vy = c0y - (double)sy, vz = c0z - (double)sz;
-    double R0 = sqrt(vx * vx + vy * vy + vz * vz);
-    double v = a.v, fs = a.fs, t0 = a.t0;
-    double n0 = rint((R0 / v - t0) * fs);
+    const double q = fma(vx, vx, fma(vy, vy, vz * vz));
+    double R0;
+    if (q > 1e-30) {
+        const double y0 = (double)rsqrtf((float)q);
+        const double y1 = y0 * fma(-0.5 * q, y0 * y0, 1.5);
+        R0 = q * y1;
+    } else {
+        R0 = sqrt(q);
+    }
+    double n0 = rint(fma(R0, a.fs_v, -a.t0fs));
     n0 = fmin(fmax(n0, -N0_CLAMP), N0_CLAMP);
-    double phi = R0 - v * (t0 + n0 / fs);
+    double phi = fma(-n0, a.dlt, R0 - a.vt0);
     PairRef r;
     r.v0x = (float)vx; r.v0y = (float)vy; r.v0z = (float)vz;
     r.R0 = (float)R0;
