@@ -207,6 +207,7 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
         }
         const PairRef* refs = refs2[cur];
         if (valid) {
+            float acc = 0.f;         // FP32 over the chunk's 32 sensors, Kahan across chunks
 #pragma unroll 2
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
@@ -234,11 +235,12 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                     if (n >= 0 && n < Nt)
                         s = fmaf(sg * delta[(size_t)(j0 + q) * Nt + n] * dE, ex2_approx(dE * dE * c2), s);
                 }
-                kA.add(s * 0.5f * invR);
+                acc = fmaf(s, invR, acc);
             }
+            kA.add(acc);
         }
     }
-    if (valid) gA[i] = kA.s;
+    if (valid) gA[i] = 0.5f * kA.s;
 }
 
 size_t adj_moment_q_bytes(const ArrDev& a, int L) { return (size_t)a.Nd * (a.Nt + L) * MOM_P * sizeof(float); }

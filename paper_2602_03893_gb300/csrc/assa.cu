@@ -14,6 +14,7 @@
 // samples over all sensors, Kahan-compensated, and writes its gradient once.
 #include <cuda.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "gpair_internal.cuh"
@@ -257,27 +258,32 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
     const int Nup = alpha * a.Nt;
     const float aInvD = (float)alpha * a.invDelta;
     constexpr int LASTW = TILE / 32 - 1;
-    KahanF kA;
-    if (warp == LASTW && lane < min(ASSA_ADJ_SC, a.Nd))
-        refs2[0][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * lane], a.xyz[3 * lane + 1], a.xyz[3 * lane + 2], a);
+    // the shared references carry alpha n0 (clamped) in place of n0
+    auto ref_fine = [&](int j) {
+        PairRef r = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        r.n0 = assa_an0(alpha, r.n0);
+        return r;
+    };
+    KahanF kA;                       // across chunks; FP32 within a chunk of 32 sensors
+    if (warp == LASTW && lane < min(ASSA_ADJ_SC, a.Nd)) refs2[0][lane] = ref_fine(lane);
     int cur = 0;
     for (int j0 = 0; j0 < a.Nd; j0 += ASSA_ADJ_SC, cur ^= 1) {
         const int nsc = min(ASSA_ADJ_SC, a.Nd - j0);
         __syncthreads();
-        if (warp == LASTW && j0 + ASSA_ADJ_SC + lane < a.Nd) {
-            const int j = j0 + ASSA_ADJ_SC + lane;
-            refs2[cur ^ 1][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
-        }
+        if (warp == LASTW && j0 + ASSA_ADJ_SC + lane < a.Nd) refs2[cur ^ 1][lane] = ref_fine(j0 + ASSA_ADJ_SC + lane);
         const PairRef* refs = refs2[cur];
         if (valid) {
+            const float* drow = dconv + (size_t)j0 * Nup;
+            float acc = 0.f;
 #pragma unroll 4
-            for (int q = 0; q < nsc; ++q) {
+            for (int q = 0; q < nsc; ++q, drow += Nup) {
                 const PairRef r = refs[q];
                 float invR, phi;
                 pair_phase_fast(r, dx, dy, dz, invR, phi);
-                const int k = assa_an0(alpha, r.n0) + (int)floorf(fmaf(phi, aInvD, 0.5f));
-                if (k >= 0 && k < Nup) kA.add(__ldg(dconv + (size_t)(j0 + q) * Nup + k) * invR);
+                const int k = r.n0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
+                if (k >= 0 && k < Nup) acc = fmaf(__ldg(drow + k), invR, acc);
             }
+            kA.add(acc);
         }
     }
     if (valid) gA[i] = kA.s;
