@@ -192,18 +192,19 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
     const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
     const int L = T.L, Nt = a.Nt;
     const float ED = (float)T.E * Delta;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // references below carry 2 (c0 - s)
     KahanF kA;
     // References are double-buffered: after each barrier the last warp forms the next chunk's
     // FP64 references while the others already work on the current chunk.
     if (warp == ADJ_THREADS / 32 - 1 && lane < min(ADJ_SC, a.Nd))
-        refs2[0][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * lane], a.xyz[3 * lane + 1], a.xyz[3 * lane + 2], a);
+        refs2[0][lane] = ref_doubled(make_ref(c0x, c0y, c0z, a.xyz[3 * lane], a.xyz[3 * lane + 1], a.xyz[3 * lane + 2], a));
     int cur = 0;
     for (int j0 = 0; j0 < a.Nd; j0 += ADJ_SC, cur ^= 1) {
         const int nsc = min(ADJ_SC, a.Nd - j0);
         __syncthreads();
         if (warp == ADJ_THREADS / 32 - 1 && j0 + ADJ_SC + lane < a.Nd) {
             const int j = j0 + ADJ_SC + lane;
-            refs2[cur ^ 1][lane] = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+            refs2[cur ^ 1][lane] = ref_doubled(make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a));
         }
         const PairRef* refs = refs2[cur];
         if (valid) {
@@ -212,7 +213,7 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
                 float invR, phi;
-                pair_phase_fast(r, dx, dy, dz, invR, phi);
+                pair_phase_pre(r, dx, dy, dz, d2, invR, phi);
                 const int m_lo = (int)ceilf((phi - ks) * invDelta);
                 const int b = r.n0 + m_lo;
                 if (b < -L || b >= Nt) continue;
@@ -228,19 +229,18 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 s = fmaf(s, e, q0.z);
                 s = fmaf(s, e, q0.y);
                 s = fmaf(s, e, q0.x);
-                const float dE = d0 - ED;              // edge position E: rare direct correction
-                const float sg = edge_sign(T, dE, ks);
-                if (sg != 0.f) {
+                if (edge_corrected(T, e)) {            // edge position E: rare direct correction
+                    const float dE = d0 - ED;
                     const int n = b + T.E;
                     if (n >= 0 && n < Nt)
-                        s = fmaf(sg * delta[(size_t)(j0 + q) * Nt + n] * dE, ex2_approx(dE * dE * c2), s);
+                        s = fmaf(edge_factor(T) * delta[(size_t)(j0 + q) * Nt + n] * dE, ex2_approx(dE * dE * c2), s);
                 }
                 acc = fmaf(s, invR, acc);
             }
             kA.add(acc);
         }
     }
-    if (valid) gA[i] = 0.5f * kA.s;
+    if (valid) gA[i] = kA.s;                 // the table carries the 1/2 of A / 2R
 }
 
 size_t adj_moment_q_bytes(const ArrDev& a, int L) { return (size_t)a.Nd * (a.Nt + L) * MOM_P * sizeof(float); }

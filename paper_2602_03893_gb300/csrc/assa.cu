@@ -258,9 +258,10 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
     const int Nup = alpha * a.Nt;
     const float aInvD = (float)alpha * a.invDelta;
     constexpr int LASTW = TILE / 32 - 1;
-    // the shared references carry alpha n0 (clamped) in place of n0
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // the shared references carry 2 (c0 - s) and alpha n0 (clamped) in place of c0 - s and n0
     auto ref_fine = [&](int j) {
-        PairRef r = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        PairRef r = ref_doubled(make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a));
         r.n0 = assa_an0(alpha, r.n0);
         return r;
     };
@@ -279,7 +280,7 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
             for (int q = 0; q < nsc; ++q, drow += Nup) {
                 const PairRef r = refs[q];
                 float invR, phi;
-                pair_phase_fast(r, dx, dy, dz, invR, phi);
+                pair_phase_pre(r, dx, dy, dz, d2, invR, phi);
                 const int k = r.n0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
                 if (k >= 0 && k < Nup) acc = fmaf(__ldg(drow + k), invR, acc);
             }

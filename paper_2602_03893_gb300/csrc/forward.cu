@@ -797,6 +797,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
     const float ks = a.k * g.sigma;
     const float rad = brick_radius(g.h);
     const float ED = (float)T.E * Delta;
+    const float efac = edge_factor(T);
     const int zlo = w - L;                 // first bin of the moment band
     // this lane's lattice offsets from the brick centre (Gaussian l = lane + 32 q)
     const float h = g.h;
@@ -855,19 +856,21 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                     const float num = (ax + ((q & 1) ? ay1 : ay0)) + oz * (2.f * r.v0z + oz);
                     float invR, phi;
                     pair_phase_num(r, num, invR, phi);
-                    const int m_lo = (int)ceilf((phi - ks) * invDelta);
-                    const int bin = r.n0 + m_lo;
-                    const bool valid = Ai != 0.f && bin >= ta && bin <= tb;
-                    key[q] = valid ? bin - ta : NB;
-                    const float d0 = fmaf(-(float)m_lo, Delta, phi);
+                    const float mf = ceilf((phi - ks) * invDelta);
+                    const int bin = r.n0 + (int)mf;
+                    const unsigned rel = (unsigned)(bin - ta);
+                    const bool valid = Ai != 0.f && rel <= (unsigned)(tb - ta);
+                    key[q] = valid ? (int)rel : NB;
+                    const float d0 = fmaf(-mf, Delta, phi);
                     ev[q] = (d0 - T.dstar) * T.inv_half;
-                    wv[q] = Ai * 0.5f * invR;
+                    wv[q] = Ai * invR;             // the table carries the 1/2
                     // edge position E: the rare pairs the table does not account for, directly
-                    const float dE = d0 - ED;
-                    const int nE = bin + T.E;
-                    const float sg = edge_sign(T, dE, ks);
-                    if (valid && sg != 0.f && nE >= w && nE <= n_hi)
-                        atomicAdd(&xband[nE - w], sg * wv[q] * dE * ex2_approx(dE * dE * c2));
+                    if (valid && edge_corrected(T, ev[q])) {
+                        const float dE = d0 - ED;
+                        const int nE = bin + T.E;
+                        if (nE >= w && nE <= n_hi)
+                            atomicAdd(&xband[nE - w], efac * wv[q] * dE * ex2_approx(dE * dE * c2));
+                    }
                     // rank within the bin (the order inside a bin only affects rounding)
                     rnk[q] = valid ? atomicAdd(&off[key[q]], 1) : 0;
                 }

@@ -357,6 +357,7 @@ bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
     T.edge_in = edge_in;
     T.dstar = (float)dstar;
     T.inv_half = (float)(2.0 / Delta);
+    T.e_thr = (float)(((double)E * Delta - k * s - dstar) * (2.0 / Delta));
     for (int m = 0; m < MOM_LMAX; ++m)
         for (int p = 0; p < MOM_P; ++p) T.c[m][p] = 0.f;
     for (int m = 0; m < L; ++m) {
@@ -370,7 +371,7 @@ bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
         for (int p = 0; p < MOM_P; ++p) {
             if (p > 0) { fact *= p; hp *= 0.5 * Delta; sp /= s; }
             const double deriv = sp * ((p & 1) ? -1.0 : 1.0) * He[p + 1] * eu;
-            T.c[m][p] = (float)(deriv * hp / fact);
+            T.c[m][p] = (float)(0.5 * deriv * hp / fact);     // with the 1/2 of A / 2R
         }
     }
     return true;

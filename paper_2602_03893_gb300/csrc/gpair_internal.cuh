@@ -94,7 +94,8 @@ struct PairRef {
 // d0 - E Delta >= -k sigma (for a fraction 2 k sigma / Delta - E of the pairs), later positions
 // never.  The table covers positions m < L: L = E + 1 when position E is inside for most pairs
 // (edge_in = 1; the pairs for which it is outside subtract its term, evaluated directly), else
-// L = E (the pairs for which it is inside add its term).
+// L = E (the pairs for which it is inside add its term).  The coefficients carry the factor 1/2 of
+// the weight A / 2R, so that a pair's weight is A / R.
 constexpr int MOM_P = 8;
 constexpr int MOM_LMAX = 128;
 struct MomentTable {
@@ -102,15 +103,18 @@ struct MomentTable {
     int E;                       // edge position
     int edge_in;                 // 1: the table covers position E
     float dstar, inv_half;       // reference phase and 2 / Delta
+    float e_thr;                 // position E is inside a pair's window iff e >= e_thr
     float c[MOM_LMAX][MOM_P];
 };
 
-// Direct-term correction of a pair at the edge position E, given dE = d0 - E Delta: the signed
-// factor (0 when the table already accounts for the pair) that multiplies w dE exp(-dE^2/2s^2).
-__device__ __forceinline__ float edge_sign(const MomentTable& T, float dE, float ks) {
-    const bool inside = dE >= -ks;
-    return inside == (T.edge_in != 0) ? 0.f : (inside ? 1.f : -1.f);
+// Edge position E is inside a pair's window when d0 >= E Delta - k sigma, i.e. e >= e_thr.  A pair
+// needs the direct correction when that differs from edge_in; its factor is then -1/2 (subtract,
+// edge_in = 1) or +1/2 (add), times (A / R) dE exp(-dE^2 / 2 sigma^2), dE = d0 - E Delta.  Forward
+// and adjoint take the decision from the same e, so they stay exact transposes.
+__device__ __forceinline__ bool edge_corrected(const MomentTable& T, float e) {
+    return (e >= T.e_thr) != (T.edge_in != 0);
 }
+__device__ __forceinline__ float edge_factor(const MomentTable& T) { return T.edge_in ? -0.5f : 0.5f; }
 
 // The paper's discretised operator (Methods, adaptive supersampling alignment): pulse centres
 // snapped to a grid ALPHA times finer than fs, pulse sampled there over |k| <= K.
@@ -195,6 +199,19 @@ __device__ __forceinline__ void pair_phase_num(const PairRef& r, float num, floa
     float rc;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(r.R0 + R));
     phi = fmaf(num, rc, r.phi0);
+}
+
+// Reference with v0 doubled (exact in FP32) for pair_phase_pre.
+__device__ __forceinline__ PairRef ref_doubled(PairRef r) {
+    r.v0x *= 2.f; r.v0y *= 2.f; r.v0z *= 2.f;
+    return r;
+}
+
+// pair_phase_fast for a thread that owns one Gaussian: r from ref_doubled, d2 = |delta|^2 of the
+// thread's offset, so that num = 2 (c0 - s) . delta + |delta|^2 takes three FMAs.
+__device__ __forceinline__ void pair_phase_pre(const PairRef& r2, float dx, float dy, float dz, float d2,
+                                               float& invR, float& phi) {
+    pair_phase_num(r2, fmaf(dx, r2.v0x, fmaf(dy, r2.v0y, fmaf(dz, r2.v0z, d2))), invR, phi);
 }
 
 __device__ __forceinline__ void pair_phase_fast(const PairRef& r, float dx, float dy, float dz,
