@@ -152,6 +152,9 @@ typedef struct {
     int T0;              /* first restart period (iterations) */
     float T_mult;        /* period multiplier (>= 1) */
     float beta1, beta2, adam_eps;
+    /* Vessel continuity regulariser (Methods: loss = data + lambda (R_H + beta R_TV), Algorithm 2);
+     * vcr_lambda = 0 disables it.  Grid Gaussians and the Adam rule only; see gpair_vcr. */
+    float vcr_lambda, vcr_beta, vcr_eps;
 } gpair_step_params;
 
 typedef struct gpair_solver gpair_solver;
@@ -164,10 +167,11 @@ gpair_status gpair_solver_create(const gpair_gaussians* g, const gpair_array* ar
                                  const gpair_step_params* params, gpair_solver** out);
 void gpair_solver_destroy(gpair_solver* s);
 
-/* One iteration of Algorithm 2 with the exact data-term gradient 2 (y - b) / N, N = Nd Nt.
- * b: device [n_sensors][n_samples].  loss_out / resid_out (host, may be NULL) receive the FP64
- * loss |y - b|^2 / N and |y - b| of the iterate entering the step; when either is non-NULL the
- * call synchronises `stream`.  The reductions are done in FP64 on the GPU. */
+/* One iteration of Algorithm 2 with the exact data-term gradient 2 (y - b) / N, N = Nd Nt, plus
+ * lambda grad R_VCR(x) when vcr_lambda > 0.  b: device [n_sensors][n_samples].  loss_out /
+ * resid_out (host, may be NULL) receive the FP64 loss |y - b|^2 / N + lambda R_VCR(x) and
+ * |y - b| of the iterate entering the step; when either is non-NULL the call synchronises
+ * `stream`.  The reductions are done in FP64 on the GPU. */
 gpair_status gpair_step(gpair_solver* s, const float* b, double* loss_out, double* resid_out,
                         void* stream);
 
@@ -201,6 +205,18 @@ const char* gpair_status_string(gpair_status s);
 gpair_status gpair_last_device_status(void* stream);
 /* Frees the scratch pool of every stream on the current device. */
 void gpair_release_scratch(void);
+
+/* gpair_vcr -- the vessel continuity regulariser (Methods, vessel continuity regularisation):
+ * R_VCR(x) = sum_i sqrt(sum_{p,q} (D_pq x)_i^2 + eps) + beta sum_i sqrt(sum_d (D_d x)_i^2 + eps) for a
+ * lattice image x (device, [nz][ny][nx], x fastest).  The paper leaves the operators open; here
+ * D_d is the central first difference (x[i+1] - x[i-1]) / 2, D_pp = x[i+1] - 2 x[i] + x[i-1], D_pq
+ * (p != q) the four-point central mixed difference / 4 (counted for (p,q) and (q,p)), with Neumann
+ * boundaries (neighbour indices clamped) and unit voxel spacing.  value_out (host, may be NULL):
+ * R_VCR in FP64 (the call then synchronises `stream`); grad (device [M], may be NULL):
+ * grad += lam * dR_VCR/dx.  Scratch: 9 M floats from the library's per-stream pool.  Errors:
+ * GPAIR_ERR_INVALID_ARG for a NULL x, non-positive sizes or eps < 0. */
+gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* grad,
+                       double* value_out, void* stream);
 
 /* ---- The paper's own discretised operator (Methods, adaptive supersampling alignment;
  * Algorithm 1), for grid Gaussians sharing one width sigma.

@@ -27,7 +27,7 @@ EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_vox
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
-           "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_version")
+           "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_vcr", "gpair_version")
 
 
 class GpairError(RuntimeError):
@@ -53,7 +53,8 @@ class _Array(ctypes.Structure):
 
 class _StepParams(ctypes.Structure):
     _fields_ = [("rule", c_int), ("npc", c_int), ("npc_eps", c_float), ("eta_max", c_float), ("eta_min", c_float),
-                ("T0", c_int), ("T_mult", c_float), ("beta1", c_float), ("beta2", c_float), ("adam_eps", c_float)]
+                ("T0", c_int), ("T_mult", c_float), ("beta1", c_float), ("beta2", c_float), ("adam_eps", c_float),
+                ("vcr_lambda", c_float), ("vcr_beta", c_float), ("vcr_eps", c_float)]
 
 
 _lib = None
@@ -88,6 +89,7 @@ def load(path: str | None = None):
         lib.gpair_release_scratch.restype = None
         lib.gpair_wait_selftest.argtypes = [c_int, P]
         lib.gpair_assa_forward.argtypes = [P, P, c_int, P, P]
+        lib.gpair_vcr.argtypes = [P, c_int, c_int, c_int, c_float, c_float, c_float, P, ctypes.POINTER(c_double), P]
         lib.gpair_assa_adjoint.argtypes = [P, P, c_int, P, P, P]
         lib.gpair_version.restype = ctypes.c_char_p
         _lib = lib
@@ -243,6 +245,17 @@ def gpair_assa_adjoint(g: Gaussians, arr: SensorArray, delta: torch.Tensor, gA: 
     return gA
 
 
+def gpair_vcr(x: torch.Tensor, dims, beta: float, eps: float = 1e-8, lam: float = 1.0, grad: torch.Tensor | None = None,
+              want_value: bool = True, stream=None):
+    """Vessel continuity regulariser of a lattice image x (dims = (nz, ny, nx), x fastest):
+    returns R_VCR(x) (FP64, synchronising) when want_value; adds lam * grad R_VCR into `grad`."""
+    nz, ny, nx = dims
+    val = c_double(0.0)
+    _check("gpair_vcr", load().gpair_vcr(_ptr(x), int(nx), int(ny), int(nz), float(beta), float(eps), float(lam),
+                                         _ptr(grad), ctypes.byref(val) if want_value else None, _stream(stream)))
+    return val.value if want_value else None
+
+
 def gpair_voxelize(g: Gaussians, out_grid: Grid, window_k: float, vol: torch.Tensor, stream=None) -> torch.Tensor:
     lib = load()
     gc_, keep = g._c()
@@ -292,10 +305,13 @@ class StepParams:
     beta1: float = 0.9
     beta2: float = 0.999
     adam_eps: float = 1e-8
+    vcr_lambda: float = 0.0      # vessel continuity regulariser weight (0: off)
+    vcr_beta: float = 0.0        # TV share of the regulariser
+    vcr_eps: float = 1e-8
 
     def _c(self) -> _StepParams:
         return _StepParams(self.rule, self.npc, self.npc_eps, self.eta_max, self.eta_min, self.T0, self.T_mult,
-                           self.beta1, self.beta2, self.adam_eps)
+                           self.beta1, self.beta2, self.adam_eps, self.vcr_lambda, self.vcr_beta, self.vcr_eps)
 
 
 class Solver:

@@ -29,6 +29,8 @@ cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const floa
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
 cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t st);
+cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* F,
+                       double* partial, double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
                                 cudaStream_t st);
@@ -594,6 +596,29 @@ gpair_status gpair_assa_adjoint(const gpair_gaussians* gi, const gpair_array* ai
     return cuda_status(launch_assa_adjoint(g, a, delta, gA, T, static_cast<float*>(scratch), st));
 }
 
+gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* grad,
+                       double* value_out, void* stream) {
+    if (!x || nx <= 0 || ny <= 0 || nz <= 0 || !(eps >= 0.f) || !std::isfinite(beta) || !std::isfinite(lam))
+        return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t M = (int64_t)nx * ny * nz;
+    const size_t fbytes = align256((size_t)M * 9 * sizeof(float));
+    void* scratch = nullptr;
+    gpair_status s = get_scratch(st, fbytes + sizeof(double) * ((size_t)red_blocks() + 1), &scratch, nullptr);
+    if (s != GPAIR_OK) return s;
+    float* F = static_cast<float*>(scratch);
+    double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + fbytes);
+    double* val = partial + red_blocks();
+    cudaError_t e = launch_vcr(x, nx, ny, nz, beta, eps, lam, F, partial, value_out ? val : nullptr, grad, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (value_out) {
+        if (cudaMemcpyAsync(value_out, val, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return GPAIR_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    }
+    return GPAIR_OK;
+}
+
 gpair_status gpair_wait_selftest(int polls, void* stream) {
     if (polls < 1 || polls > (1 << 20)) return GPAIR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -634,6 +659,7 @@ struct gpair_solver {
     double* red = nullptr;   // reduction partials (2 * red_blocks) + results (4)
     void* fwd_scratch = nullptr;
     void* qbuf = nullptr;    // expansion table of the amplitude adjoint (grid Gaussians)
+    float* vcrF = nullptr;   // regulariser fields, 9 M floats (vcr_lambda > 0)
     int* status = nullptr;
     FwdPlan plan;
     // Profiling (gpair_solver_profile): per recorded step six events on the step's stream --
@@ -674,6 +700,11 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     if (prm->rule == GPAIR_RULE_ADAM &&
         (!(prm->beta1 >= 0.f && prm->beta1 < 1.f) || !(prm->beta2 >= 0.f && prm->beta2 < 1.f) || !(prm->adam_eps >= 0.f)))
         return GPAIR_ERR_INVALID_ARG;
+    const bool vcr = prm->vcr_lambda != 0.f;
+    if (!std::isfinite(prm->vcr_lambda) || prm->vcr_lambda < 0.f || (vcr && (!(prm->vcr_eps >= 0.f) ||
+                                                                          !std::isfinite(prm->vcr_beta))))
+        return GPAIR_ERR_INVALID_ARG;
+    if (vcr && (prm->rule != GPAIR_RULE_ADAM || !g.grid)) return GPAIR_ERR_UNSUPPORTED;
     gpair_solver* S = new gpair_solver();
     S->g = g;
     S->a = a;
@@ -688,7 +719,8 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               cudaMalloc(&S->red, sizeof(double) * (2 * red_blocks() + 8)) == cudaSuccess &&
               cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
               (adjoint_q_bytes(g, a) == 0 || cudaMalloc(&S->qbuf, adjoint_q_bytes(g, a)) == cudaSuccess) &&
-              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess &&
+              (!vcr || cudaMalloc(&S->vcrF, M * 9 * sizeof(float)) == cudaSuccess);
     if (!ok) {
         cudaGetLastError();
         gpair_solver_destroy(S);
@@ -711,7 +743,7 @@ void gpair_solver_destroy(gpair_solver* S) {
     if (!S) return;
     cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
     cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
-    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status);
+    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->vcrF);
     for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
     delete S;
 }
@@ -769,6 +801,10 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
         if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr, S->qbuf)) !=
             GPAIR_OK)
             return s;
+        if (S->vcrF &&   // grad_x += lambda grad R_VCR(x); R_VCR(x) into res[4]
+            (e = launch_vcr(S->x, S->g.nx, S->g.ny, S->g.nz, S->p.vcr_beta, S->p.vcr_eps, S->p.vcr_lambda, S->vcrF,
+                            partial, res + 4, S->gx, st)) != cudaSuccess)
+            return cuda_status(e);
         const int tt = S->t + 1;
         const double c1 = 1.0 - std::pow((double)S->p.beta1, tt), c2 = 1.0 - std::pow((double)S->p.beta2, tt);
         const float eta = (float)cawr(S->t, S->p);
@@ -796,11 +832,12 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
     }
     S->t += 1;
     if (loss_out || resid_out) {
-        double h = 0.0;
-        if (cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+        double h[5] = {0, 0, 0, 0, 0};
+        if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
-        if (loss_out) *loss_out = h / (double)N;
-        if (resid_out) *resid_out = std::sqrt(h);
+        const double reg = S->vcrF ? (double)S->p.vcr_lambda * h[4] : 0.0;
+        if (loss_out) *loss_out = h[0] / (double)N + reg;
+        if (resid_out) *resid_out = std::sqrt(h[0]);
     }
     return GPAIR_OK;
 }

@@ -163,6 +163,138 @@ cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M
 
 int red_blocks() { return RED_BLOCKS; }
 
+// ---- vessel continuity regulariser (Methods: R_VCR = R_H + beta R_TV) on a lattice image --------
+// Readings of the unspecified parts: central first differences (x[i+1] - x[i-1]) / 2; second
+// differences x[i+1] - 2 x[i] + x[i-1] and the four-point mixed stencil / 4 (counted twice in the
+// Frobenius sum, D_pq = D_qp); Neumann boundaries (neighbour indices clamped per axis); unit voxel
+// spacing; eps inside each square root.  Image x fastest.
+
+__device__ __forceinline__ int64_t vox(int ix, int iy, int iz, int nx, int ny) {
+    return ((int64_t)iz * ny + iy) * nx + ix;
+}
+
+// Pass 1: per voxel the derivative terms and the weighted fields
+//   F_k = m_k (D_k x) / sqrt(sH + eps)  (k = xx, yy, zz, xy, xz, yz; m = 1, 1, 1, 2, 2, 2),
+//   F_{6+d} = beta (D_d x) / sqrt(sT + eps),
+// sH = sum_{p,q} (D_pq x)^2, sT = sum_d (D_d x)^2; partial[blk] = sum sqrt(sH + eps) + beta sqrt(sT + eps).
+__global__ void __launch_bounds__(RED_THREADS)
+vcr_fields_kernel(const float* __restrict__ x, int nx, int ny, int nz, float beta, float eps, float* __restrict__ F,
+                  double* __restrict__ partial) {
+    __shared__ double red[RED_THREADS / 32];
+    const int64_t M = (int64_t)nx * ny * nz;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx);
+        const int64_t r = i / nx;
+        const int iy = (int)(r % ny), iz = (int)(r / ny);
+        const int xm = max(ix - 1, 0), xp = min(ix + 1, nx - 1);
+        const int ym = max(iy - 1, 0), yp = min(iy + 1, ny - 1);
+        const int zm = max(iz - 1, 0), zp = min(iz + 1, nz - 1);
+        auto at = [&](int a, int b, int c) { return __ldg(x + vox(a, b, c, nx, ny)); };
+        const float c0 = x[i];
+        const float vxp = at(xp, iy, iz), vxm = at(xm, iy, iz);
+        const float vyp = at(ix, yp, iz), vym = at(ix, ym, iz);
+        const float vzp = at(ix, iy, zp), vzm = at(ix, iy, zm);
+        const float d1x = 0.5f * (vxp - vxm), d1y = 0.5f * (vyp - vym), d1z = 0.5f * (vzp - vzm);
+        const float hxx = (vxp - c0) + (vxm - c0), hyy = (vyp - c0) + (vym - c0), hzz = (vzp - c0) + (vzm - c0);
+        const float hxy = 0.25f * ((at(xp, yp, iz) - at(xp, ym, iz)) - (at(xm, yp, iz) - at(xm, ym, iz)));
+        const float hxz = 0.25f * ((at(xp, iy, zp) - at(xp, iy, zm)) - (at(xm, iy, zp) - at(xm, iy, zm)));
+        const float hyz = 0.25f * ((at(ix, yp, zp) - at(ix, yp, zm)) - (at(ix, ym, zp) - at(ix, ym, zm)));
+        const float sH = hxx * hxx + hyy * hyy + hzz * hzz + 2.f * (hxy * hxy + hxz * hxz + hyz * hyz);
+        const float sT = d1x * d1x + d1y * d1y + d1z * d1z;
+        const float rH = sqrtf(sH + eps), rT = sqrtf(sT + eps);
+        const float wH = 1.f / rH, wT = beta / rT;
+        F[i] = wH * hxx;
+        F[M + i] = wH * hyy;
+        F[2 * M + i] = wH * hzz;
+        F[3 * M + i] = 2.f * wH * hxy;
+        F[4 * M + i] = 2.f * wH * hxz;
+        F[5 * M + i] = 2.f * wH * hyz;
+        F[6 * M + i] = wT * d1x;
+        F[7 * M + i] = wT * d1y;
+        F[8 * M + i] = wT * d1z;
+        acc += (double)rH + (double)beta * (double)rT;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Stencil entries of the nine operators: field k, neighbour offset, coefficient.
+struct VcrEntry {
+    signed char k, ox, oy, oz;
+    float c;
+};
+__constant__ VcrEntry c_vcr[27] = {
+    {0, 1, 0, 0, 1.f}, {0, 0, 0, 0, -2.f}, {0, -1, 0, 0, 1.f},
+    {1, 0, 1, 0, 1.f}, {1, 0, 0, 0, -2.f}, {1, 0, -1, 0, 1.f},
+    {2, 0, 0, 1, 1.f}, {2, 0, 0, 0, -2.f}, {2, 0, 0, -1, 1.f},
+    {3, 1, 1, 0, .25f}, {3, 1, -1, 0, -.25f}, {3, -1, 1, 0, -.25f}, {3, -1, -1, 0, .25f},
+    {4, 1, 0, 1, .25f}, {4, 1, 0, -1, -.25f}, {4, -1, 0, 1, -.25f}, {4, -1, 0, -1, .25f},
+    {5, 0, 1, 1, .25f}, {5, 0, 1, -1, -.25f}, {5, 0, -1, 1, -.25f}, {5, 0, -1, -1, .25f},
+    {6, 1, 0, 0, .5f}, {6, -1, 0, 0, -.5f},
+    {7, 0, 1, 0, .5f}, {7, 0, -1, 0, -.5f},
+    {8, 0, 0, 1, .5f}, {8, 0, 0, -1, -.5f},
+};
+
+// Coordinates i in [0, n) with clamp(i + o) == j (o in {-1, 0, 1}): at most two.
+__device__ __forceinline__ int vcr_preimage(int j, int o, int n, int* out) {
+    int c = 0;
+    for (int i = j - o - 1; i <= j - o + 1; ++i)
+        if (i >= 0 && i < n && min(max(i + o, 0), n - 1) == j) out[c++] = i;
+    return c;
+}
+
+// Pass 2: g[j] += lam (sum_k D_k^T F_k)[j].  (D^T F)[j] = sum over the stencil entries (o, c) of
+// c F[i] over every i whose clamped neighbour i + o is j; inside the volume that is i = j - o.
+__global__ void __launch_bounds__(RED_THREADS, 4)
+vcr_grad_kernel(const float* __restrict__ F, int nx, int ny, int nz, float lam, float* __restrict__ g) {
+    const int64_t M = (int64_t)nx * ny * nz;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
+        const int jx = (int)(j % nx);
+        const int64_t r = j / nx;
+        const int jy = (int)(r % ny), jz = (int)(r / ny);
+        float acc = 0.f;
+        if (jx > 0 && jx < nx - 1 && jy > 0 && jy < ny - 1 && jz > 0 && jz < nz - 1) {
+#pragma unroll
+            for (int e = 0; e < 27; ++e) {
+                const VcrEntry E = c_vcr[e];
+                acc = fmaf(E.c, __ldg(F + E.k * M + (j - (E.ox + (int64_t)E.oy * nx + (int64_t)E.oz * nx * ny))), acc);
+            }
+        } else {
+            for (int e = 0; e < 27; ++e) {
+                const VcrEntry E = c_vcr[e];
+                int px[2], py[2], pz[2];
+                const int cx = vcr_preimage(jx, E.ox, nx, px), cy = vcr_preimage(jy, E.oy, ny, py),
+                          cz = vcr_preimage(jz, E.oz, nz, pz);
+                float s = 0.f;
+                for (int a = 0; a < cx; ++a)
+                    for (int b = 0; b < cy; ++b)
+                        for (int c = 0; c < cz; ++c) s += __ldg(F + E.k * M + vox(px[a], py[b], pz[c], nx, ny));
+                acc = fmaf(E.c, s, acc);
+            }
+        }
+        g[j] = fmaf(lam, acc, g[j]);
+    }
+}
+
+// value_out (device, may be NULL): R_VCR(x) in FP64.  g (may be NULL): g += lam grad R_VCR(x).
+// F: 9 M floats of scratch; partial: RED_BLOCKS doubles.
+cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* F,
+                       double* partial, double* value_out, float* g, cudaStream_t st) {
+    vcr_fields_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, nx, ny, nz, beta, eps, F, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (value_out) {
+        finish_kernel<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 1, 1, value_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (g) {
+        vcr_grad_kernel<<<RED_BLOCKS * 4, RED_THREADS, 0, st>>>(F, nx, ny, nz, lam, g);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 // Failure-detection self-test: one warp waits on a shared-memory barrier that nothing completes,
 // with a bound of `polls` polls; the wait gives up, the timeout goes into the status word and the
 // kernel returns normally (no trap, nothing in flight).

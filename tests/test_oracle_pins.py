@@ -448,3 +448,59 @@ def test_assa_converges_to_the_windowed_forward_as_n_min_grows():
     (a1, e1), (a2, e2), (a3, e3) = errs
     assert e2 < e1 * 2.0 * a1 / a2 and e3 < e2 * 2.0 * a2 / a3, errs
     assert all(0.005 < e * a < 0.05 for a, e in errs), errs     # error x alpha roughly constant
+
+
+# ---------------------------------------------------------------- VCR regulariser
+
+def test_vcr_gradient_matches_central_differences():
+    from oracle import vcr
+
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.0, 1.0, (4, 5, 6))
+    beta = 0.7
+    _, g = vcr.value_and_grad(x, beta)
+    h = 1e-6
+    for idx in [(0, 0, 0), (3, 4, 5), (1, 2, 3), (2, 0, 5), (0, 4, 2), (3, 1, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (vcr.value_and_grad(xp, beta)[0] - vcr.value_and_grad(xm, beta)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, g[idx])
+
+
+def test_vcr_constant_image():
+    from oracle import vcr
+
+    x = np.full((3, 4, 5), 2.5)
+    val, g = vcr.value_and_grad(x, 0.3, eps=1e-8)
+    assert abs(val - x.size * 1e-4 * 1.3) <= 1e-12 * val
+    assert np.abs(g).max() == 0.0
+
+
+def test_vcr_linear_ramp_closed_form():
+    """x = a * ix: central differences give a inside and a / 2 on the two x faces (clamped
+    neighbour); second differences vanish inside and are +a / -a on the faces; no mixed terms."""
+    from oracle import vcr
+
+    nz, ny, nx, a, eps, beta = 3, 4, 6, 0.8, 1e-8, 0.5
+    x = a * np.broadcast_to(np.arange(nx, dtype=np.float64), (nz, ny, nx))
+    val, _ = vcr.value_and_grad(x, beta, eps)
+    rows = ny * nz
+    R_TV = rows * ((nx - 2) * np.sqrt(a * a + eps) + 2 * np.sqrt(a * a / 4 + eps))
+    R_H = rows * ((nx - 2) * np.sqrt(eps) + 2 * np.sqrt(a * a + eps))
+    assert abs(val - (R_H + beta * R_TV)) <= 1e-12 * val
+
+
+def test_vcr_mixed_derivative_of_a_bilinear_image():
+    from oracle import vcr
+
+    nz, ny, nx = 3, 5, 6
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x = (ix * iy).astype(np.float64)
+    first, hess = vcr.operators(x.shape)
+    Dxy = hess[3][0] @ x.ravel()
+    inner = ((ix > 0) & (ix < nx - 1) & (iy > 0) & (iy < ny - 1)).ravel()
+    assert np.allclose(Dxy[inner], 1.0)
+    assert hess[3][1] == 2.0
+    Dxx = (hess[0][0] @ x.ravel())[((ix > 0) & (ix < nx - 1)).ravel()]
+    assert np.allclose(Dxx, 0.0)
