@@ -42,6 +42,17 @@ LAUNCHES_PER_STEP = 9           # npc, slab info, forward, slab reduce, resid, f
 ASSA_NMIN = 25                  # the paper's minimum number of fine samples across the pulse
 
 
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0               # the recipe's fallback
+
+
+HBM_GBS = _measured_hbm()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -51,7 +62,7 @@ def parse():
     p.add_argument("--workload", default="paper", choices=["paper", "mid", "tiny"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sensors", type=int, default=32)
-    p.add_argument("--no-assa", action="store_true", help="skip timing the paper's ASSA operator")
+    p.add_argument("--no-assa", action="store_true", help="skip timing the paper's ASSA operator and the regulariser")
     return p.parse_args()
 
 
@@ -372,6 +383,28 @@ def main():
                 "paper_ms": {"forward": 37.41, "adjoint": 4.99, "hardware": "RTX 5090 (the paper's)"},
                 "includes": "forward: slab info + kernel + slab reduction; adjoint: correlated residual + kernel"}
 
+    # ---- the vessel continuity regulariser (value + gradient) on the same image, HBM-bound
+    vcr = None
+    if not args.no_assa:
+        x_img = solver.gpair_solver_image()
+        gv = torch.zeros_like(x_img)
+        dims = (g.nz, g.ny, g.nx)
+        for _ in range(2):
+            _lib.gpair_vcr(x_img, dims, 0.5, 1e-8, 1e-3, gv, want_value=False)
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            _lib.gpair_vcr(x_img, dims, 0.5, 1e-8, 1e-3, gv, want_value=False)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms = v0.elapsed_time(v1) / args.steps
+        # x in, 9 fields out and back in, gradient read and written: 4 (1 + 9 + 9 + 2) bytes per voxel
+        vbytes = 4.0 * (1 + 9 + 9 + 2) * w.M
+        vcr = {"ms": vms, "alg_bytes": vbytes, "achieved_GBs": vbytes / (vms / 1e3) / 1e9,
+               "peak_GBs": HBM_GBS, "frac": vbytes / (vms / 1e3) / 1e9 / HBM_GBS,
+               "includes": "fields + FP64 block partials + transposed-stencil gradient (no host sync)"}
+
     clocks = sampler.summary()
     pairs, samples = work_units(w)
     fwd_avg = fwd_ms / max(nrec, 1) / 1e3
@@ -421,7 +454,7 @@ def main():
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
                               "step_device": step_ms / max(nrec, 1)},
-                "roofline": roofline, "assa": assa, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "assa": assa, "vcr": vcr, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     solver.close()
