@@ -214,7 +214,8 @@ void gpair_release_scratch(void);
  * boundaries (neighbour indices clamped) and unit voxel spacing.  value_out (host, may be NULL):
  * R_VCR in FP64 (the call then synchronises `stream`); grad (device [M], may be NULL):
  * grad += lam * dR_VCR/dx.  Scratch: 9 M floats from the library's per-stream pool.  Errors:
- * GPAIR_ERR_INVALID_ARG for a NULL x, non-positive sizes or eps < 0. */
+ * GPAIR_ERR_INVALID_ARG for a NULL x, non-positive sizes or eps < 0; GPAIR_ERR_UNSUPPORTED when
+ * ny nz >= 2^31. */
 gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* grad,
                        double* value_out, void* stream);
 

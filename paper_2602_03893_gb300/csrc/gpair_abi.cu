@@ -600,6 +600,7 @@ gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float
                        double* value_out, void* stream) {
     if (!x || nx <= 0 || ny <= 0 || nz <= 0 || !(eps >= 0.f) || !std::isfinite(beta) || !std::isfinite(lam))
         return GPAIR_ERR_INVALID_ARG;
+    if ((int64_t)ny * nz > (int64_t)INT32_MAX) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t M = (int64_t)nx * ny * nz;
     const size_t fbytes = align256((size_t)M * 9 * sizeof(float));
@@ -704,7 +705,8 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     if (!std::isfinite(prm->vcr_lambda) || prm->vcr_lambda < 0.f || (vcr && (!(prm->vcr_eps >= 0.f) ||
                                                                           !std::isfinite(prm->vcr_beta))))
         return GPAIR_ERR_INVALID_ARG;
-    if (vcr && (prm->rule != GPAIR_RULE_ADAM || !g.grid)) return GPAIR_ERR_UNSUPPORTED;
+    if (vcr && (prm->rule != GPAIR_RULE_ADAM || !g.grid || (int64_t)g.ny * g.nz > (int64_t)INT32_MAX))
+        return GPAIR_ERR_UNSUPPORTED;
     gpair_solver* S = new gpair_solver();
     S->g = g;
     S->a = a;

@@ -183,10 +183,11 @@ vcr_fields_kernel(const float* __restrict__ x, int nx, int ny, int nz, float bet
     __shared__ double red[RED_THREADS / 32];
     const int64_t M = (int64_t)nx * ny * nz;
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % nx);
-        const int64_t r = i / nx;
-        const int iy = (int)(r % ny), iz = (int)(r / ny);
+    // blocks stride over (y, z) rows, threads over x: no per-voxel index division
+    for (int row = blockIdx.x; row < ny * nz; row += gridDim.x)
+    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+        const int iy = row % ny, iz = row / ny;
+        const int64_t i = (int64_t)row * nx + ix;
         const int xm = max(ix - 1, 0), xp = min(ix + 1, nx - 1);
         const int ym = max(iy - 1, 0), yp = min(iy + 1, ny - 1);
         const int zm = max(iz - 1, 0), zp = min(iz + 1, nz - 1);
@@ -249,10 +250,10 @@ __device__ __forceinline__ int vcr_preimage(int j, int o, int n, int* out) {
 __global__ void __launch_bounds__(RED_THREADS, 4)
 vcr_grad_kernel(const float* __restrict__ F, int nx, int ny, int nz, float lam, float* __restrict__ g) {
     const int64_t M = (int64_t)nx * ny * nz;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
-        const int jx = (int)(j % nx);
-        const int64_t r = j / nx;
-        const int jy = (int)(r % ny), jz = (int)(r / ny);
+    for (int row = blockIdx.x; row < ny * nz; row += gridDim.x)
+    for (int jx = threadIdx.x; jx < nx; jx += blockDim.x) {
+        const int jy = row % ny, jz = row / ny;
+        const int64_t j = (int64_t)row * nx + jx;
         float acc = 0.f;
         if (jx > 0 && jx < nx - 1 && jy > 0 && jy < ny - 1 && jz > 0 && jz < nz - 1) {
 #pragma unroll
@@ -289,7 +290,7 @@ cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (g) {
-        vcr_grad_kernel<<<RED_BLOCKS * 4, RED_THREADS, 0, st>>>(F, nx, ny, nz, lam, g);
+        vcr_grad_kernel<<<RED_BLOCKS * 8, RED_THREADS, 0, st>>>(F, nx, ny, nz, lam, g);
         e = cudaGetLastError();
     }
     return e;
