@@ -28,6 +28,14 @@ extern "C" {
 
 typedef uint16_t gpair_bf16;
 
+/* Convolution path: 1 (default) runs gpair_conv3d_fwd / _dgrad on the 5th-generation tensor cores
+ * (tcgen05 MMAs with the accumulator in tensor memory) whenever Cin and Cout are multiples of 16,
+ * Cout <= 128 or a multiple of 128, and the tensors are 16-byte aligned; 0 uses the mma.sync
+ * kernel for every shape.  Any other mode only queries.  Returns the path in force. */
+int gpair_unet_tensor_path(int mode);
+/* 1 if a bounded wait of the tensor-core convolution gave up since the last call (then cleared). */
+int gpair_unet_tc_status(void);
+
 /* out = act(conv(in, w) + bias): bias FP32 [Cout] or NULL; relu != 0 applies max(., 0). */
 gpair_status gpair_conv3d_fwd(const gpair_bf16* in, int D, int H, int W, int Cin, const gpair_bf16* w,
                               const float* bias, int Cout, int taps, int relu, gpair_bf16* out, void* stream);

@@ -373,15 +373,37 @@ gpair_status st(cudaError_t e) { return e == cudaSuccess ? GPAIR_OK : GPAIR_ERR_
 
 bool dims_ok(int D, int H, int W, int C) { return D > 0 && H > 0 && W > 0 && C > 0; }
 
+int g_tensor_path = 1;   // 1: tcgen05 kernel where eligible; 0: mma.sync kernel only
+
 }  // namespace
 
+namespace gp {
+cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Cin, const uint16_t* w,
+                                 const float* bias, int Cout, int taps, int relu, uint16_t* out, cudaStream_t st);
+int conv_tc_status_and_clear();
+}  // namespace gp
+
 extern "C" {
+
+int gpair_unet_tensor_path(int mode) {
+    if (mode == 0 || mode == 1) g_tensor_path = mode;
+    return g_tensor_path;
+}
+
+int gpair_unet_tc_status(void) { return gp::conv_tc_status_and_clear(); }
 
 gpair_status gpair_conv3d_fwd(const gpair_bf16* in, int D, int H, int W, int Cin, const gpair_bf16* w,
                               const float* bias, int Cout, int taps, int relu, gpair_bf16* out, void* stream) {
     if (!in || !w || !out || !dims_ok(D, H, W, Cin) || Cout <= 0 || (taps != 1 && taps != 27)) return GPAIR_ERR_INVALID_ARG;
     if (Cin % 16 != 0 || Cout % 8 != 0) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g_tensor_path) {
+        const cudaError_t e = gp::launch_conv3d_fwd_tc(reinterpret_cast<const uint16_t*>(in), D, H, W, Cin,
+                                                       reinterpret_cast<const uint16_t*>(w), bias, Cout, taps, relu,
+                                                       reinterpret_cast<uint16_t*>(out), s);
+        if (e != cudaErrorNotSupported) return st(e);
+        cudaGetLastError();     // not eligible: the mma.sync kernel below
+    }
     const int64_t nv = (int64_t)D * H * W;
     const unsigned gx = (unsigned)((nv + 16 * CONV_MT * 4 - 1) / (16 * CONV_MT * 4));
     if (Cout % 64 == 0)

@@ -46,6 +46,10 @@ def _unet_lib():
         lib.gpair_unpack_output.argtypes = [P, i64, i32, f32, i32, P, P]
         lib.gpair_mse_loss.argtypes = [P, P, i64, i32, P, P, P]
         lib.gpair_adam_bf16.argtypes = [P, P, P, P, P, i64, f32, f32, f32, f32, i32, P]
+        lib.gpair_unet_tensor_path.argtypes = [i32]
+        lib.gpair_unet_tensor_path.restype = i32
+        lib.gpair_unet_tc_status.argtypes = []
+        lib.gpair_unet_tc_status.restype = i32
         _bound = True
     return lib
 
@@ -64,6 +68,16 @@ def _ck(name, code):
 
 
 # ---------------------------------------------------------------- thin wrappers (same names)
+
+def gpair_unet_tensor_path(mode: int = -1) -> int:
+    """1: convolutions on the tcgen05 tensor cores where eligible (default); 0: mma.sync only;
+    other values query.  Returns the path in force."""
+    return int(_unet_lib().gpair_unet_tensor_path(int(mode)))
+
+
+def gpair_unet_tc_status() -> int:
+    return int(_unet_lib().gpair_unet_tc_status())
+
 
 def gpair_conv3d_fwd(x, dims, Cin, w, b, Cout, taps, relu, out):
     D, H, W = dims

@@ -35,8 +35,19 @@ def _close(got, ref, rel=2e-2):
 @pytest.mark.parametrize("dims,cin,cout,taps,relu", [((6, 5, 7), 16, 16, 27, True), ((4, 6, 5), 48, 32, 27, False),
                                                       ((5, 4, 9), 32, 128, 27, True), ((3, 3, 3), 16, 16, 27, False),
                                                       ((7, 5, 6), 64, 48, 27, True), ((4, 4, 4), 16, 16, 1, False),
-                                                      ((6, 6, 6), 192, 64, 27, True)])
-def test_conv_fwd_dgrad_wgrad(dims, cin, cout, taps, relu):
+                                                      ((6, 6, 6), 192, 64, 27, True), ((9, 8, 7), 32, 256, 27, True)])
+@pytest.mark.parametrize("path", [1, 0])
+def test_conv_fwd_dgrad_wgrad(dims, cin, cout, taps, relu, path):
+    """path 1: the tcgen05 kernel (every shape here is eligible), path 0: the mma.sync kernel."""
+    prev = unet.gpair_unet_tensor_path(path)
+    try:
+        _conv_case(dims, cin, cout, taps, relu)
+        assert unet.gpair_unet_tc_status() == 0
+    finally:
+        unet.gpair_unet_tensor_path(prev)
+
+
+def _conv_case(dims, cin, cout, taps, relu):
     gen = torch.Generator().manual_seed(cin * 7 + cout)
     nv = int(np.prod(dims))
     x = _bf((nv, cin), gen)
@@ -64,6 +75,32 @@ def test_conv_fwd_dgrad_wgrad(dims, cin, cout, taps, relu):
     unet.gpair_conv3d_wgrad(xd, gd, dims, cin, cout, taps, dw, db)
     _close(dw.cpu(), wr.grad, rel=1e-4)
     _close(db.cpu(), dout.double().sum(0), rel=1e-4)
+
+
+def test_tensor_core_paths_agree_on_the_unet_layers():
+    """The tcgen05 and mma.sync convolutions on the U-Net's own layer shapes (128 x 128 x 64 level
+    halved to keep the test short): both accumulate in FP32, so their BF16 outputs differ by at most
+    a few units in the last place."""
+    gen = torch.Generator().manual_seed(11)
+    dims = (16, 32, 32)
+    nv = int(np.prod(dims))
+    for cin, cout in [(16, 16), (32, 32), (64, 64), (128, 128), (256, 128), (32, 16)]:
+        x = _bf((nv, cin), gen).cuda()
+        w = _bf((cout, 27, cin), gen, scale=0.1).cuda()
+        b = torch.randn(cout, generator=gen).float().cuda()
+        outs = []
+        for path in (1, 0):
+            prev = unet.gpair_unet_tensor_path(path)
+            y = torch.empty((nv, cout), dtype=torch.bfloat16, device="cuda")
+            unet.gpair_conv3d_fwd(x, dims, cin, w, b, cout, 27, True, y)
+            torch.cuda.synchronize()
+            unet.gpair_unet_tensor_path(prev)
+            outs.append(y.float())
+        assert unet.gpair_unet_tc_status() == 0
+        d = (outs[0] - outs[1]).abs()
+        scale = outs[1].abs().max().item()
+        assert d.max().item() <= 2e-2 * scale, (cin, cout, d.max().item(), scale)
+        assert (d > 0).float().mean().item() < 0.2, (cin, cout)
 
 
 def test_pool_up_concat_relu():
