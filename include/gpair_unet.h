@@ -28,10 +28,11 @@ extern "C" {
 
 typedef uint16_t gpair_bf16;
 
-/* Convolution path: 1 (default) runs gpair_conv3d_fwd / _dgrad on the 5th-generation tensor cores
- * (tcgen05 MMAs with the accumulator in tensor memory) whenever Cin and Cout are multiples of 16,
- * Cout <= 128 or a multiple of 128, and the tensors are 16-byte aligned; 0 uses the mma.sync
- * kernel for every shape.  Any other mode only queries.  Returns the path in force. */
+/* Convolution path of gpair_conv3d_fwd / _dgrad.  The 5th-generation tensor-core kernel (tcgen05
+ * MMAs, accumulator in tensor memory) takes shapes with Cin and Cout multiples of 16, Cout <= 128
+ * or a multiple of 128, and 16-byte aligned tensors.  Mode 1 (default) uses it for Cout >= 64,
+ * where it measured faster than the mma.sync kernel; mode 2 for every eligible shape; mode 0
+ * never.  Other values only query.  Returns the mode in force. */
 int gpair_unet_tensor_path(int mode);
 /* 1 if a bounded wait of the tensor-core convolution gave up since the last call (then cleared). */
 int gpair_unet_tc_status(void);

@@ -373,7 +373,9 @@ gpair_status st(cudaError_t e) { return e == cudaSuccess ? GPAIR_OK : GPAIR_ERR_
 
 bool dims_ok(int D, int H, int W, int C) { return D > 0 && H > 0 && W > 0 && C > 0; }
 
-int g_tensor_path = 1;   // 1: tcgen05 kernel where eligible; 0: mma.sync kernel only
+// 1: tcgen05 kernel for Cout >= 64 (where it measured faster); 2: tcgen05 for every eligible
+// shape; 0: mma.sync kernel only.
+int g_tensor_path = 1;
 
 }  // namespace
 
@@ -386,7 +388,7 @@ int conv_tc_status_and_clear();
 extern "C" {
 
 int gpair_unet_tensor_path(int mode) {
-    if (mode == 0 || mode == 1) g_tensor_path = mode;
+    if (mode >= 0 && mode <= 2) g_tensor_path = mode;
     return g_tensor_path;
 }
 
@@ -397,7 +399,7 @@ gpair_status gpair_conv3d_fwd(const gpair_bf16* in, int D, int H, int W, int Cin
     if (!in || !w || !out || !dims_ok(D, H, W, Cin) || Cout <= 0 || (taps != 1 && taps != 27)) return GPAIR_ERR_INVALID_ARG;
     if (Cin % 16 != 0 || Cout % 8 != 0) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (g_tensor_path) {
+    if (g_tensor_path == 2 || (g_tensor_path == 1 && Cout >= 64)) {
         const cudaError_t e = gp::launch_conv3d_fwd_tc(reinterpret_cast<const uint16_t*>(in), D, H, W, Cin,
                                                        reinterpret_cast<const uint16_t*>(w), bias, Cout, taps, relu,
                                                        reinterpret_cast<uint16_t*>(out), s);

@@ -9,7 +9,8 @@
 // weights' rows) with cp.async, in the canonical K-major layout without swizzle (core matrices of
 // 8 rows x 16 bytes; adjacent core matrices along K are 128 bytes apart, along M/N Kc * 16 bytes).
 // One thread issues the stage's MMAs (K = 16 each) and commits them to the stage buffer's
-// mbarrier; the next stage's gather into the other buffer overlaps them.  Every wait is bounded.
+// mbarrier; the gathers of the next stages, in a ring of shared buffers, overlap them.  Every wait
+// is bounded.
 // The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31),
 // adds the bias, applies the ReLU and stores BF16.
 #include <cuda_bf16.h>
@@ -78,6 +79,11 @@ __device__ __forceinline__ uint16_t f2bf_rn(float f) {
 }
 
 // out[v][co0 + c] = act(bias + sum_{t, ci} in[v + off(t)][ci] w[co0 + c][t][ci]), c < NT.
+// TC_STAGES shared buffers: the gathers of up to TC_STAGES - 1 stages are in flight (one cp.async
+// group each) while the tensor cores work; a buffer is refilled once the commit of the MMAs that
+// read it has arrived on its mbarrier.
+constexpr int TC_STAGES = 4;
+
 __global__ void __launch_bounds__(TC_THREADS)
 conv3d_fwd_tc_kernel(const uint16_t* __restrict__ in, int D, int H, int W, int Cin, const uint16_t* __restrict__ w,
                      const float* __restrict__ bias, int Cout, int NT, int ncols, int taps, int relu, int Kc,
@@ -89,10 +95,9 @@ conv3d_fwd_tc_kernel(const uint16_t* __restrict__ in, int D, int H, int W, int C
     const int co0 = blockIdx.y * NT;
     const int K = taps * Cin;
     const uint32_t aBytes = (uint32_t)TC_M * Kc * 2, bBytes = (uint32_t)NT * Kc * 2;
-    unsigned char* Abuf[2] = {sm, sm + aBytes};
-    unsigned char* Bbuf[2] = {sm + 2 * aBytes, sm + 2 * aBytes + bBytes};
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * aBytes + 2 * bBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const uint32_t stBytes = aBytes + bBytes;               // stage buffer: A tile then B tile
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TC_STAGES * stBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES);
     const uint32_t lbo = 128, sbo = (uint32_t)(Kc / 8) * 128;
 
     if (warp == 0) {
@@ -101,8 +106,7 @@ conv3d_fwd_tc_kernel(const uint16_t* __restrict__ in, int D, int H, int W, int C
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int q = 0; q < TC_STAGES; ++q) mbar_init(&mbar[q], 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -116,37 +120,53 @@ conv3d_fwd_tc_kernel(const uint16_t* __restrict__ in, int D, int H, int W, int C
     const int nchunk = Cin / Kc, S = taps * nchunk;
     const uint32_t idesc = tc_idesc(NT, TC_M);
     bool ok = true;
-    for (int s = 0; s < S; ++s) {
-        const int b = s & 1;
-        // the MMAs of stage s - 2 read this buffer: wait for their commit
-        if (s >= 2 && !mbar_wait(&mbar[b], (uint32_t)(((s - 2) >> 1) & 1))) ok = false;
-        const int t = s / nchunk, c0 = (s - t * nchunk) * Kc;
-        int dz = 0, dy = 0, dx = 0;
-        if (taps == 27) { dz = t / 9 - 1; dy = (t / 3) % 3 - 1; dx = t % 3 - 1; }
-        const int x = vx + dx, y = vy + dy, z = vz + dz;
-        const bool inb = vok && x >= 0 && x < W && y >= 0 && y < H && z >= 0 && z < D;
-        const uint16_t* asrc = inb ? in + (((int64_t)z * H + y) * W + x) * Cin + c0 : in;
-        unsigned char* arow = Abuf[b] + (tid >> 3) * sbo + (tid & 7) * 16;
-        for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(arow + kc * 128, asrc + kc * 8, inb ? 16u : 0u);
-        for (int r = tid; r < NT; r += TC_THREADS) {
-            const uint16_t* bsrc = w + (int64_t)(co0 + r) * K + (int64_t)t * Cin + c0;
-            unsigned char* brow = Bbuf[b] + (r >> 3) * sbo + (r & 7) * 16;
-            for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(brow + kc * 128, bsrc + kc * 8, 16u);
+
+    // gather stage s into its buffer (one cp.async group; empty groups past the last stage keep
+    // the group count uniform)
+    auto gather = [&](int s) {
+        if (s < S) {
+            unsigned char* buf = sm + (s % TC_STAGES) * stBytes;
+            const int t = s / nchunk, c0 = (s - t * nchunk) * Kc;
+            int dz = 0, dy = 0, dx = 0;
+            if (taps == 27) { dz = t / 9 - 1; dy = (t / 3) % 3 - 1; dx = t % 3 - 1; }
+            const int x = vx + dx, y = vy + dy, z = vz + dz;
+            const bool inb = vok && x >= 0 && x < W && y >= 0 && y < H && z >= 0 && z < D;
+            const uint16_t* asrc = inb ? in + (((int64_t)z * H + y) * W + x) * Cin + c0 : in;
+            unsigned char* arow = buf + (tid >> 3) * sbo + (tid & 7) * 16;
+            for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(arow + kc * 128, asrc + kc * 8, inb ? 16u : 0u);
+            for (int r = tid; r < NT; r += TC_THREADS) {
+                const uint16_t* bsrc = w + (int64_t)(co0 + r) * K + (int64_t)t * Cin + c0;
+                unsigned char* brow = buf + aBytes + (r >> 3) * sbo + (r & 7) * 16;
+                for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(brow + kc * 128, bsrc + kc * 8, 16u);
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    };
+    for (int s = 0; s < TC_STAGES - 1; ++s) gather(s);
+    for (int s = 0; s < S; ++s) {
+        // stage s's group is complete once at most TC_STAGES - 2 newer groups are pending
+        asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // generic writes -> tensor-core reads
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
+            unsigned char* buf = sm + (s % TC_STAGES) * stBytes;
             for (int ks = 0; ks < Kc / 16; ++ks)
-                tc_mma(tmem, smem_desc(Abuf[b] + ks * 2 * lbo, lbo, sbo), smem_desc(Bbuf[b] + ks * 2 * lbo, lbo, sbo),
+                tc_mma(tmem, smem_desc(buf + ks * 2 * lbo, lbo, sbo), smem_desc(buf + aBytes + ks * 2 * lbo, lbo, sbo),
                        idesc, (s > 0 || ks > 0) ? 1u : 0u);
-            tc_commit(&mbar[b]);
+            tc_commit(&mbar[s % TC_STAGES]);
         }
+        // refill the buffer of stage s - 1 with stage s + TC_STAGES - 1 once its MMAs are done
+        const int sn = s + TC_STAGES - 1;
+        if (sn < S && s >= 1) {
+            const int sp = s - 1;
+            if (!mbar_wait(&mbar[sp % TC_STAGES], (uint32_t)((sp / TC_STAGES) & 1))) ok = false;
+        }
+        gather(sn);
     }
     // the last commit covers every MMA issued before it
-    if (!mbar_wait(&mbar[(S - 1) & 1], (uint32_t)(((S - 1) >> 1) & 1))) ok = false;
+    if (!mbar_wait(&mbar[(S - 1) % TC_STAGES], (uint32_t)(((S - 1) / TC_STAGES) & 1))) ok = false;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     tc_fence_after();
     if (!ok) atomicMax(&g_conv_tc_status, 1);
     for (int cc = 0; cc < NT; cc += 16) {
@@ -180,9 +200,9 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
     const int NT = Cout <= 128 ? Cout : (Cout % 128 == 0 ? 128 : 0);
     if (NT == 0) return cudaErrorNotSupported;
     if (((uintptr_t)in | (uintptr_t)w | (uintptr_t)out) & 15) return cudaErrorNotSupported;
-    const int Kc = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
+    const int Kc = Cin % 32 == 0 ? 32 : 16;
     const int ncols = NT <= 32 ? 32 : (NT <= 64 ? 64 : 128);
-    const size_t smem = 2 * ((size_t)TC_M * Kc * 2 + (size_t)NT * Kc * 2) + 32;
+    const size_t smem = TC_STAGES * ((size_t)TC_M * Kc * 2 + (size_t)NT * Kc * 2) + 8 * TC_STAGES + 16;
     cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t nv = (int64_t)D * H * W;
