@@ -238,6 +238,22 @@ gpair_status gpair_assa_forward(const gpair_gaussians* g, const gpair_array* arr
 gpair_status gpair_assa_adjoint(const gpair_gaussians* g, const gpair_array* arr, int n_min, const float* delta,
                                 float* gA, void* stream);
 
+/* ---- Image metrics of reconstructions (Results, Table 1: PSNR, SSIM, MSE on the volume and on its
+ * maximum amplitude projection along z).  The paper gives no formulas; these follow the common
+ * definitions.
+ *
+ * gpair_zmap: out[y][x] = max_z vol[z][y][x] (device, vol [nz][ny][nx], out [ny][nx]).
+ * gpair_image_metrics: x and ref (device, [nz][ny][nx], nz = 1 for an image) -> out (host, 3
+ * doubles): MSE, PSNR = 10 log10(data_range^2 / MSE) and the mean SSIM (Wang et al., 2004) with a
+ * uniform window of `win` samples per axis (odd, >= 3), sample (N / (N - 1)) variances and
+ * covariance, C1 = (0.01 data_range)^2, C2 = (0.03 data_range)^2, over the positions whose window
+ * lies inside; FP64 sums.  Synchronises `stream`; scratch 10 M floats from the per-stream pool.
+ * Errors: GPAIR_ERR_INVALID_ARG for NULL pointers, even or < 3 win, data_range <= 0;
+ * GPAIR_ERR_UNSUPPORTED when an axis (z only if nz > 1) is shorter than win. */
+gpair_status gpair_zmap(const float* vol, int nx, int ny, int nz, float* out, void* stream);
+gpair_status gpair_image_metrics(const float* x, const float* ref, int nx, int ny, int nz, int win, float data_range,
+                                 double* out, void* stream);
+
 /* gpair_wait_selftest -- exercises the failure-detection path of the bounded waits.  Launches one
  * warp that waits on a shared-memory barrier nothing completes, giving up after `polls` polls
  * (1 <= polls <= 2^20, else GPAIR_ERR_INVALID_ARG, nothing launched); the kernel records a timeout

@@ -27,7 +27,8 @@ EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_vox
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
-           "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_vcr", "gpair_version")
+           "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_vcr", "gpair_zmap",
+           "gpair_image_metrics", "gpair_version")
 
 
 class GpairError(RuntimeError):
@@ -89,6 +90,8 @@ def load(path: str | None = None):
         lib.gpair_release_scratch.restype = None
         lib.gpair_wait_selftest.argtypes = [c_int, P]
         lib.gpair_assa_forward.argtypes = [P, P, c_int, P, P]
+        lib.gpair_zmap.argtypes = [P, c_int, c_int, c_int, P, P]
+        lib.gpair_image_metrics.argtypes = [P, P, c_int, c_int, c_int, c_int, c_float, ctypes.POINTER(c_double), P]
         lib.gpair_vcr.argtypes = [P, c_int, c_int, c_int, c_float, c_float, c_float, P, ctypes.POINTER(c_double), P]
         lib.gpair_assa_adjoint.argtypes = [P, P, c_int, P, P, P]
         lib.gpair_version.restype = ctypes.c_char_p
@@ -254,6 +257,24 @@ def gpair_vcr(x: torch.Tensor, dims, beta: float, eps: float = 1e-8, lam: float 
     _check("gpair_vcr", load().gpair_vcr(_ptr(x), int(nx), int(ny), int(nz), float(beta), float(eps), float(lam),
                                          _ptr(grad), ctypes.byref(val) if want_value else None, _stream(stream)))
     return val.value if want_value else None
+
+
+def gpair_zmap(vol: torch.Tensor, dims, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Maximum amplitude projection along z of a (nz, ny, nx) volume."""
+    nz, ny, nx = dims
+    out = out if out is not None else torch.empty((ny, nx), device=vol.device, dtype=torch.float32)
+    _check("gpair_zmap", load().gpair_zmap(_ptr(vol), nx, ny, nz, _ptr(out), _stream(stream)))
+    return out
+
+
+def gpair_image_metrics(x: torch.Tensor, ref: torch.Tensor, dims, win: int = 7, data_range: float = 1.0,
+                        stream=None) -> dict:
+    """MSE, PSNR (dB) and mean SSIM of x against ref; dims = (nz, ny, nx), nz = 1 for an image."""
+    nz, ny, nx = dims
+    out = (c_double * 3)()
+    _check("gpair_image_metrics", load().gpair_image_metrics(_ptr(x), _ptr(ref), nx, ny, nz, int(win),
+                                                             float(data_range), out, _stream(stream)))
+    return {"mse": out[0], "psnr": out[1], "ssim": out[2]}
 
 
 def gpair_voxelize(g: Gaussians, out_grid: Grid, window_k: float, vol: torch.Tensor, stream=None) -> torch.Tensor:

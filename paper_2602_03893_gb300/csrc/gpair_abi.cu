@@ -29,6 +29,10 @@ cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const floa
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_npc(const float* z, float* x, int64_t M, int npc, float eps, cudaStream_t st);
 cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t st);
+cudaError_t launch_zmap(const float* vol, int nx, int ny, int nz, float* out, cudaStream_t st);
+size_t ssim_scratch_bytes(int64_t M);
+cudaError_t launch_ssim_sum(const float* x, const float* y, int nx, int ny, int nz, int win, float range, void* scratch,
+                            double* out, cudaStream_t st);
 cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* F,
                        double* partial, double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
@@ -617,6 +621,39 @@ gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float
             return GPAIR_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
     }
+    return GPAIR_OK;
+}
+
+gpair_status gpair_zmap(const float* vol, int nx, int ny, int nz, float* out, void* stream) {
+    if (!vol || !out || nx <= 0 || ny <= 0 || nz <= 0) return GPAIR_ERR_INVALID_ARG;
+    return cuda_status(launch_zmap(vol, nx, ny, nz, out, static_cast<cudaStream_t>(stream)));
+}
+
+gpair_status gpair_image_metrics(const float* x, const float* ref, int nx, int ny, int nz, int win, float data_range,
+                                 double* out, void* stream) {
+    if (!x || !ref || !out || nx <= 0 || ny <= 0 || nz <= 0 || win < 3 || (win & 1) == 0 || !(data_range > 0.f))
+        return GPAIR_ERR_INVALID_ARG;
+    if (nx < win || ny < win || (nz > 1 && nz < win) || (int64_t)ny * nz > (int64_t)INT32_MAX)
+        return GPAIR_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t M = (int64_t)nx * ny * nz;
+    void* scratch = nullptr;
+    const size_t sbytes = align256(ssim_scratch_bytes(M));
+    gpair_status s = get_scratch(st, sbytes + sizeof(double) * (2 * (size_t)red_blocks() + 4), &scratch, nullptr);
+    if (s != GPAIR_OK) return s;
+    double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + sbytes);
+    double* res = partial + 2 * red_blocks();
+    cudaError_t e = launch_reduce2(x, ref, nullptr, M, partial, res, st);          // res[0] = sum (x - ref)^2
+    if (e == cudaSuccess) e = launch_ssim_sum(x, ref, nx, ny, nz, win, data_range, scratch, res + 2, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    double h[3];
+    if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    const int p = (win - 1) / 2;
+    const double inner = (double)(nx - 2 * p) * (ny - 2 * p) * (nz > 1 ? nz - 2 * p : 1);
+    out[0] = h[0] / (double)M;
+    out[1] = 10.0 * std::log10((double)data_range * data_range / out[0]);
+    out[2] = h[2] / inner;
     return GPAIR_OK;
 }
 

@@ -504,3 +504,39 @@ def test_vcr_mixed_derivative_of_a_bilinear_image():
     assert hess[3][1] == 2.0
     Dxx = (hess[0][0] @ x.ravel())[((ix > 0) & (ix < nx - 1)).ravel()]
     assert np.allclose(Dxx, 0.0)
+
+
+# ---------------------------------------------------------------- image metrics (Table 1)
+
+def test_metrics_closed_forms():
+    from oracle import metrics
+
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 1, (9, 10, 11))
+    assert abs(metrics.ssim(x, x) - 1.0) < 1e-12
+    assert abs(metrics.psnr(x + 0.1, x) - 20.0) < 1e-9          # MSE 0.01, range 1
+    # constant image against a shifted one: only the luminance term remains
+    a, c, C1 = 0.4, 0.25, (0.01) ** 2
+    ones = np.ones((9, 9, 9))
+    expect = (2 * a * (a + c) + C1) / (a * a + (a + c) ** 2 + C1)
+    assert abs(metrics.ssim(a * ones, (a + c) * ones) - expect) < 1e-12
+    # the projection, brute force
+    m = metrics.zmap(x)
+    for iy, ix in [(0, 0), (3, 7), (9, 10)]:
+        assert m[iy, ix] == max(x[z, iy, ix] for z in range(x.shape[0]))
+
+
+def test_ssim_window_by_brute_force():
+    """One interior position of a 2-D SSIM map, from its window's samples directly."""
+    from oracle import metrics
+
+    rng = np.random.default_rng(6)
+    x, y = rng.uniform(0, 1, (12, 13)), rng.uniform(0, 1, (12, 13))
+    win, C1, C2 = 7, 1e-4, 9e-4
+    # SSIM over a 7 x 7 image is the single value of its one interior position
+    xs, ys = x[:7, :7], y[:7, :7]
+    mx, my = xs.mean(), ys.mean()
+    sx, sy = xs.var(ddof=1), ys.var(ddof=1)
+    sxy = ((xs - mx) * (ys - my)).sum() / (xs.size - 1)
+    expect = (2 * mx * my + C1) * (2 * sxy + C2) / ((mx * mx + my * my + C1) * (sx + sy + C2))
+    assert abs(metrics.ssim(xs, ys, win=win) - expect) < 1e-12
