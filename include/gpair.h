@@ -231,7 +231,7 @@ gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float
  * arr->window_k is not used (the pulse support is the paper's 3-sigma rule, N_half samples).
  * Adjoint: gA_i = sum_j (1 / r_ij) sum_n h[alpha n - k_ij] delta_j[n], the exact transpose.
  * Layouts as gpair_forward / gpair_adjoint; gA has M entries.  Errors: GPAIR_ERR_UNSUPPORTED for
- * free-centre Gaussians, K > 256 or alpha N_t >= 2^30; GPAIR_ERR_INVALID_ARG for n_min < 1 or
+ * free-centre Gaussians, K > 256, alpha N_t >= 2^30 or N_d alpha N_t >= 2^31; GPAIR_ERR_INVALID_ARG for n_min < 1 or
  * NULL buffers.  Asynchronous on `stream`; scratch from the library's per-stream pool (the
  * adjoint's correlated residual: N_d alpha N_t floats). */
 gpair_status gpair_assa_forward(const gpair_gaussians* g, const gpair_array* arr, int n_min, float* y, void* stream);

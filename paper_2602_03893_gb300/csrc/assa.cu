@@ -242,7 +242,7 @@ size_t assa_dconv_smem(const AssaTable& T) { return (size_t)((255 + 2 * T.K) / T
 __global__ void __launch_bounds__(TILE)
 assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __grid_constant__ AssaTable T,
                 float* __restrict__ gA) {
-    __shared__ PairRef refs2[2][ASSA_ADJ_SC];
+    __shared__ AdjRef refs2[2][ASSA_ADJ_SC];
     const int64_t t = blockIdx.x;
     const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
     const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
@@ -259,11 +259,10 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
     const float aInvD = (float)alpha * a.invDelta;
     constexpr int LASTW = TILE / 32 - 1;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    // the shared references carry 2 (c0 - s) and alpha n0 (clamped) in place of c0 - s and n0
+    // the shared references carry alpha n0 (clamped) and the sensor's row j alpha Nt of dconv
     auto ref_fine = [&](int j) {
-        PairRef r = ref_doubled(make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a));
-        r.n0 = assa_an0(alpha, r.n0);
-        return r;
+        const PairRef r = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
+        return adj_ref(r, assa_an0(alpha, r.n0), j * Nup);
     };
     KahanF kA;                       // across chunks; FP32 within a chunk of 32 sensors
     if (warp == LASTW && lane < min(ASSA_ADJ_SC, a.Nd)) refs2[0][lane] = ref_fine(lane);
@@ -272,17 +271,16 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
         const int nsc = min(ASSA_ADJ_SC, a.Nd - j0);
         __syncthreads();
         if (warp == LASTW && j0 + ASSA_ADJ_SC + lane < a.Nd) refs2[cur ^ 1][lane] = ref_fine(j0 + ASSA_ADJ_SC + lane);
-        const PairRef* refs = refs2[cur];
+        const AdjRef* refs = refs2[cur];
         if (valid) {
-            const float* drow = dconv + (size_t)j0 * Nup;
             float acc = 0.f;
 #pragma unroll 4
-            for (int q = 0; q < nsc; ++q, drow += Nup) {
-                const PairRef r = refs[q];
+            for (int q = 0; q < nsc; ++q) {
+                const AdjRef r = refs[q];
                 float invR, phi;
-                pair_phase_pre(r, dx, dy, dz, d2, invR, phi);
+                pair_phase_r(r, dx, dy, dz, d2, invR, phi);
                 const int k = r.n0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
-                if (k >= 0 && k < Nup) acc = fmaf(__ldg(drow + k), invR, acc);
+                if ((unsigned)k < (unsigned)Nup) acc = fmaf(__ldg(dconv + (size_t)(unsigned)(r.row + k)), invR, acc);
             }
             kA.add(acc);
         }

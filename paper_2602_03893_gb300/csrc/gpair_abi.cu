@@ -535,6 +535,7 @@ bool make_assa_table(const GaussDev& g, const ArrDev& a, int n_min, AssaTable& T
     int alpha = (int)std::ceil(((double)(n_min - 1) / 2.0) / (double)nh);
     if (alpha < 1) alpha = 1;
     if ((int64_t)alpha * nh > ASSA_KMAX || (int64_t)alpha * a.Nt >= (1LL << 30)) return false;
+    if ((int64_t)a.Nd * alpha * a.Nt >= (int64_t)INT32_MAX) return false;   // 32-bit row offsets in the adjoint
     T.alpha = alpha;
     T.n_half = nh;
     T.K = alpha * nh;

@@ -201,6 +201,40 @@ __device__ __forceinline__ void pair_phase_num(const PairRef& r, float num, floa
     phi = fmaf(num, rc, r.phi0);
 }
 
+// Shared per-(tile, sensor) reference of the adjoints that give each thread one Gaussian: 2 (c0 - s)
+// (doubled exactly), R0, phi0, the reference sample n0 plus a kernel-specific offset, and the
+// sensor's first entry in the kernel's table; 32 bytes, read as two 16-byte loads.
+struct __align__(16) AdjRef {
+    float v2x, v2y, v2z, R0;
+    float phi0;
+    int n0;      // n0 + the kernel's offset
+    int row;     // the sensor's row in the kernel's table
+    int pad;
+};
+
+__device__ __forceinline__ AdjRef adj_ref(const PairRef& r, int n0, int row) {
+    AdjRef a;
+    a.v2x = 2.f * r.v0x; a.v2y = 2.f * r.v0y; a.v2z = 2.f * r.v0z;
+    a.R0 = r.R0;
+    a.phi0 = r.phi0;
+    a.n0 = n0;
+    a.row = row;
+    a.pad = 0;
+    return a;
+}
+
+// Phase and 1 / R of the pair of a thread's Gaussian (offset with |delta|^2 = d2) and a reference.
+__device__ __forceinline__ void pair_phase_r(const AdjRef& r, float dx, float dy, float dz, float d2, float& invR,
+                                             float& phi) {
+    const float num = fmaf(dx, r.v2x, fmaf(dy, r.v2y, fmaf(dz, r.v2z, d2)));
+    const float R2 = fmaf(r.R0, r.R0, num);
+    invR = rsqrtf(R2);
+    const float R = R2 * invR;
+    float rc;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(r.R0 + R));
+    phi = fmaf(num, rc, r.phi0);
+}
+
 // Reference with v0 doubled (exact in FP32) for pair_phase_pre.
 __device__ __forceinline__ PairRef ref_doubled(PairRef r) {
     r.v0x *= 2.f; r.v0y *= 2.f; r.v0z *= 2.f;
