@@ -145,6 +145,7 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
 // so one table of L-tap correlations per sensor replaces the per-sample evaluation.
 
 // Q[j][b + L][p] for window starts b in [-L, N_t): the residual is zero outside the record.
+template <int P>
 __global__ void __launch_bounds__(256)
 adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ MomentTable T, float* __restrict__ Q) {
     extern __shared__ float sd[];   // residual samples b0 .. b0 + 256 + L
@@ -161,11 +162,11 @@ adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ Mo
     if (b >= Nt) return;
     float acc[MOM_P];
 #pragma unroll
-    for (int p = 0; p < MOM_P; ++p) acc[p] = 0.f;
+    for (int p = 0; p < MOM_P; ++p) acc[p] = 0.f;     // acc[p >= P] stays 0
     for (int m = 0; m < L; ++m) {
         const float dl = sd[threadIdx.x + m];
 #pragma unroll
-        for (int p = 0; p < MOM_P; ++p) acc[p] = fmaf(dl, T.c[m][p], acc[p]);
+        for (int p = 0; p < P; ++p) acc[p] = fmaf(dl, T.c[m][p], acc[p]);
     }
     float4* dst = reinterpret_cast<float4*>(Q + ((size_t)j * (Nt + L) + (b + L)) * MOM_P);
     dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -173,6 +174,7 @@ adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ Mo
 }
 
 // One CTA per brick of 256 grid Gaussians, one thread per Gaussian, all sensors in chunks of 32.
+template <int P>
 __global__ void __launch_bounds__(ADJ_THREADS)
 adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const float* __restrict__ Q,
                   const __grid_constant__ MomentTable T, float* __restrict__ gA) {
@@ -221,8 +223,9 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 const float e = (d0 - T.dstar) * T.inv_half;
                 const float4* qp = reinterpret_cast<const float4*>(Q + ((size_t)(j0 + q) * (Nt + L) + (b + L)) * MOM_P);
                 const float4 q0 = __ldg(qp), q1 = __ldg(qp + 1);
-                float s = q1.w;
-                s = fmaf(s, e, q1.z);
+                float s;
+                if constexpr (P == 8) s = fmaf(q1.w, e, q1.z);
+                else s = q1.z;
                 s = fmaf(s, e, q1.y);
                 s = fmaf(s, e, q1.x);
                 s = fmaf(s, e, q0.w);
@@ -248,11 +251,13 @@ size_t adj_moment_q_bytes(const ArrDev& a, int L) { return (size_t)a.Nd * (a.Nt 
 cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const float* delta, float* gA,
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st) {
     dim3 qgrid((a.Nt + T.L + 255) / 256, a.Nd);
-    adj_q_kernel<<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
+    if (T.P == 7) adj_q_kernel<7><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
+    else adj_q_kernel<8><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    adj_moment_kernel<<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
+    if (T.P == 7) adj_moment_kernel<7><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
+    else adj_moment_kernel<8><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     return e;

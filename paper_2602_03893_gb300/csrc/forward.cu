@@ -699,12 +699,17 @@ struct FwdMomSmem {
 constexpr size_t FWDM_HDR = (sizeof(FwdMomSmem) + 127) & ~(size_t)127;
 
 // Per-warp shared memory: sorted records (e, w) [TILE] | bin offsets [TB + 2] | moment band
-// [MOM_P][LB + L] | direct-term band [LB].
-__host__ __device__ __forceinline__ size_t fwdm_warp_bytes(int TB, int LB, int L) {
-    return (size_t)TILE * 8 + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15) + (size_t)(LB + L) * MOM_P * 4 +
+// [P][LB + L] | direct-term band [LB], each part a multiple of 16 bytes so that every warp's
+// records stay 8-byte aligned (with P = 7 and LB + L odd the band alone is not).
+__host__ __device__ __forceinline__ size_t fwdm_band_floats(int LB, int L, int P) {
+    return (((size_t)(LB + L) * P + 3) & ~(size_t)3);
+}
+__host__ __device__ __forceinline__ size_t fwdm_warp_bytes(int TB, int LB, int L, int P) {
+    return (size_t)TILE * 8 + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15) + fwdm_band_floats(LB, L, P) * 4 +
            (((size_t)LB * 4 + 15) & ~(size_t)15);
 }
 
+template <int P>
 __global__ void __launch_bounds__(FWD_THREADS, 3)
 fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
                   int2* __restrict__ rows, int LB, int TB, int* status, int use_tma,
@@ -716,11 +721,12 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = T.L;
     const int ZS = LB + L;                 // bins of the moment band
-    unsigned char* wbase = smem_raw + FWDM_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L);
+    static_assert(P == 7 || P == 8, "7 or 8 moments");
+    unsigned char* wbase = smem_raw + FWDM_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L, P);
     float2* rec = reinterpret_cast<float2*>(wbase);
     int* off = reinterpret_cast<int*>(wbase + (size_t)TILE * 8);
     float* Z = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(off) + (((size_t)(TB + 2) * 4 + 15) & ~(size_t)15));
-    float* xband = Z + (size_t)ZS * MOM_P;
+    float* xband = Z + fwdm_band_floats(LB, L, P);
 
     const int slab = blockIdx.y;
     const int j = blockIdx.x * FWD_SPC + warp;
@@ -761,7 +767,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
         }
         fence_mbar_init();
     }
-    for (int q = lane; q < ZS * MOM_P; q += 32) Z[q] = 0.f;
+    for (int q = lane; q < ZS * P; q += 32) Z[q] = 0.f;
     for (int q = lane; q < LB; q += 32) xband[q] = 0.f;
     __syncthreads();
 
@@ -905,16 +911,15 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                 for (int bb = lane; bb < NB; bb += 32) {
                     const int start = off[bb], end = off[bb + 1];
                     if (start == end) continue;
-                    float M[MOM_P];
+                    float M[P];
 #pragma unroll
-                    for (int p = 0; p < MOM_P; ++p) M[p] = 0.f;
-                    static_assert(MOM_P == 8, "the power tree below is written for 8 moments");
+                    for (int p = 0; p < P; ++p) M[p] = 0.f;
 #pragma unroll 2
                     for (int i = start; i < end; ++i) {
                         const float2 rr = rec[i];
                         const float e1 = rr.x, wq = rr.y;
                         const float e2 = e1 * e1, e4 = e2 * e2;
-                        const float e3 = e2 * e1, e5 = e4 * e1, e6 = e4 * e2, e7 = e4 * e3;
+                        const float e3 = e2 * e1, e5 = e4 * e1, e6 = e4 * e2;
                         M[0] += wq;
                         M[1] = fmaf(wq, e1, M[1]);
                         M[2] = fmaf(wq, e2, M[2]);
@@ -922,11 +927,11 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                         M[4] = fmaf(wq, e4, M[4]);
                         M[5] = fmaf(wq, e5, M[5]);
                         M[6] = fmaf(wq, e6, M[6]);
-                        M[7] = fmaf(wq, e7, M[7]);
+                        if constexpr (P == 8) M[P - 1] = fmaf(wq, e4 * e3, M[P - 1]);
                     }
                     float* zp = Z + (ta + bb - zlo);
 #pragma unroll
-                    for (int p = 0; p < MOM_P; ++p) zp[(size_t)p * ZS] += M[p];
+                    for (int p = 0; p < P; ++p) zp[(size_t)p * ZS] += M[p];
                 }
                 __syncwarp();
             }
@@ -963,7 +968,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
             for (int m = 0; m < L; ++m) {
                 const float* zm = zb - m;
 #pragma unroll
-                for (int p = 0; p < MOM_P; ++p) y = fmaf(T.c[m][p], zm[(size_t)p * ZS], y);
+                for (int p = 0; p < P; ++p) y = fmaf(T.c[m][p], zm[(size_t)p * ZS], y);
             }
             prow[q] = y;
         }
@@ -1037,12 +1042,13 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
         // window-start bins of one brick: phases within its radius of phi0, so at most
         // 2 rad / Delta + 7 bins (floor/ceil and the -2/+2 margins)
         const int TBm = ((int)std::ceil(2.0 * brick_radius(g.h) * a.invDelta) + 8 + 3) & ~3;
-        const size_t msm = FWDM_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TBm, LB, mom->L);
+        const size_t msm = FWDM_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TBm, LB, mom->L, mom->P);
         if (msm <= 227 * 1024) {
-            e = cudaFuncSetAttribute(fwd_moment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+            auto kern = mom->P == 7 ? fwd_moment_kernel<7> : fwd_moment_kernel<8>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
             if (e != cudaSuccess) return e;
-            fwd_moment_kernel<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TBm, status, tmap != nullptr,
-                                                              *(tmap ? tmap : &null_tmap()), *mom);
+            kern<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TBm, status, tmap != nullptr,
+                                                 *(tmap ? tmap : &null_tmap()), *mom);
             return cudaGetLastError();
         }
     }

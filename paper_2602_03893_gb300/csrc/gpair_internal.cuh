@@ -95,10 +95,13 @@ struct PairRef {
 // never.  The table covers positions m < L: L = E + 1 when position E is inside for most pairs
 // (edge_in = 1; the pairs for which it is outside subtract its term, evaluated directly), else
 // L = E (the pairs for which it is inside add its term).  The coefficients carry the factor 1/2 of
-// the weight A / 2R, so that a pair's weight is A / R.
+// the weight A / 2R, so that a pair's weight is A / R.  The host keeps the first P = 7 terms when
+// their truncation error, evaluated over every position and offset, stays below 3e-7 of the
+// pulse's peak, and all MOM_P = 8 otherwise.
 constexpr int MOM_P = 8;
 constexpr int MOM_LMAX = 128;
 struct MomentTable {
+    int P;                       // terms used (7 or 8; c[m][p] = 0 for p >= P)
     int L;                       // positions covered by the expansion
     int E;                       // edge position
     int edge_in;                 // 1: the table covers position E

@@ -56,6 +56,15 @@ def test_window_edge_position_in_and_out_of_expansion(sigma_scale):
     _check(w, delta, full=False, A=w.A)
 
 
+@pytest.mark.parametrize("h", [0.2e-3, 0.08e-3])
+def test_moment_expansion_with_seven_and_eight_terms(h):
+    g = synth.centred_grid(16, 16, 12, h)
+    A = np.random.default_rng(13).uniform(0.0, 1.0, g.M).astype(np.float32)
+    w = synth.Workload("terms", g, synth.cap_sensors(64, 20e-3, 160.0), 1024, A=A)
+    delta = np.random.default_rng(14).normal(size=(w.Nd, w.Nt)).astype(np.float32)
+    _check(w, delta, full=False, A=w.A)
+
+
 def test_adjoint_identity_on_gpu():
     w = synth.tiny(1)
     rng = np.random.default_rng(4)

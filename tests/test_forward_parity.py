@@ -50,6 +50,15 @@ def test_window_edge_position_in_and_out_of_expansion(sigma_scale):
     _check(w)
 
 
+@pytest.mark.parametrize("h", [0.2e-3, 0.08e-3])
+def test_moment_expansion_with_seven_and_eight_terms(h):
+    """Delta / sigma = 0.19 keeps 7 terms of the sub-sample expansion; 0.47 needs all 8."""
+    g = synth.centred_grid(16, 16, 12, h)
+    A = np.random.default_rng(13).uniform(0.0, 1.0, g.M).astype(np.float32)
+    w = synth.Workload("terms", g, synth.cap_sensors(64, 20e-3, 160.0), 1024, A=A)
+    _check(w)
+
+
 def test_free_gaussians_per_gaussian_sigma():
     g = synth.centred_grid(24, 20, 16, 0.1e-3)
     free = synth.free_gaussians(g, 31, A=np.random.default_rng(3).uniform(0, 1, g.M))
