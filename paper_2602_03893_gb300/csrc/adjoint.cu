@@ -194,6 +194,7 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
     const float c2 = -0.72134752044448170368f / (g.sigma * g.sigma);
     const int L = T.L, Nt = a.Nt;
     const float ED = (float)T.E * Delta;
+    const float ksi = ks * invDelta;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // references below carry 2 (c0 - s)
     KahanF kA;
     // References are double-buffered: after each barrier the last warp forms the next chunk's
@@ -216,10 +217,10 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 const PairRef r = refs[q];
                 float invR, phi;
                 pair_phase_pre(r, dx, dy, dz, d2, invR, phi);
-                const int m_lo = (int)ceilf((phi - ks) * invDelta);
-                const int b = r.n0 + m_lo;
+                const float mf = ceilf(fmaf(phi, invDelta, -ksi));   // as the forward
+                const int b = r.n0 + (int)mf;
                 if (b < -L || b >= Nt) continue;
-                const float d0 = fmaf(-(float)m_lo, Delta, phi);
+                const float d0 = fmaf(-mf, Delta, phi);
                 const float e = (d0 - T.dstar) * T.inv_half;
                 const float4* qp = reinterpret_cast<const float4*>(Q + ((size_t)(j0 + q) * (Nt + L) + (b + L)) * MOM_P);
                 const float4 q0 = __ldg(qp), q1 = __ldg(qp + 1);

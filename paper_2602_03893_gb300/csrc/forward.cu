@@ -804,6 +804,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
     const float rad = brick_radius(g.h);
     const float ED = (float)T.E * Delta;
     const float efac = edge_factor(T);
+    const float ksi = ks * invDelta;       // k sigma in samples (same rounding as the adjoint)
     const int zlo = w - L;                 // first bin of the moment band
     // this lane's lattice offsets from the brick centre (Gaussian l = lane + 32 q)
     const float h = g.h;
@@ -862,7 +863,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                     const float num = (ax + ((q & 1) ? ay1 : ay0)) + oz * (2.f * r.v0z + oz);
                     float invR, phi;
                     pair_phase_num(r, num, invR, phi);
-                    const float mf = ceilf((phi - ks) * invDelta);
+                    const float mf = ceilf(fmaf(phi, invDelta, -ksi));   // first sample with d <= k sigma
                     const int bin = r.n0 + (int)mf;
                     const unsigned rel = (unsigned)(bin - ta);
                     const bool valid = Ai != 0.f && rel <= (unsigned)(tb - ta);

@@ -69,6 +69,38 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), ctypes.c_void_p(1024), None) == 1
 
 
+def test_size_limits_and_new_entry_points_rejected_on_the_host(lib):
+    """The documented limits (N_t <= 2^27, N_d <= 65535) and the argument checks of the ASSA,
+    regulariser and metric entry points return their status before any CUDA call."""
+    grid = _lib._Grid(4, 4, 4, 0.0, 0.0, 0.0, 1e-4, 1e-4)
+    g = _lib._Gaussians()
+    g.M, g.A, g.grid = 64, 1024, ctypes.pointer(grid)
+    a = _lib._Array()
+    a.n_sensors, a.xyz, a.sound_speed, a.fs, a.n_samples, a.window_k = 1, 1024, 1500.0, 40e6, 16, 3.0
+    y = ctypes.c_void_p(1024)
+    a.n_samples = (1 << 27) + 1
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), y, None) == 5
+    a.n_samples, a.n_sensors = 16, 65536
+    assert lib.gpair_forward(ctypes.byref(g), ctypes.byref(a), y, None) == 5
+    a.n_sensors = 1
+    lib.gpair_assa_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gpair_assa_forward(ctypes.byref(g), ctypes.byref(a), 0, y, None) == 1          # n_min < 1
+    soa = _lib._Gaussians()
+    soa.M, soa.A, soa.cx, soa.cy, soa.cz, soa.sigma = 64, 1024, 1024, 1024, 1024, 1024
+    assert lib.gpair_assa_forward(ctypes.byref(soa), ctypes.byref(a), 25, y, None) == 5      # one width needed
+    lib.gpair_vcr.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gpair_vcr(y, 0, 4, 4, 0.5, 1e-8, 1.0, None, None, None) == 1
+    assert lib.gpair_vcr(y, 4, 4, 4, 0.5, -1.0, 1.0, None, None, None) == 1
+    lib.gpair_image_metrics.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+    out = (ctypes.c_double * 3)()
+    assert lib.gpair_image_metrics(y, y, 8, 8, 8, 4, 1.0, out, None) == 1                      # even window
+    assert lib.gpair_image_metrics(y, y, 8, 8, 5, 7, 1.0, out, None) == 5                      # z shorter than it
+    lib.gpair_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    assert lib.gpair_wait_selftest(0, None) == 1
+
+
 def test_product_package_never_imports_the_oracle():
     pkg = os.path.join(ROOT, "paper_2602_03893_gb300")
     for dirpath, _, files in os.walk(pkg):
