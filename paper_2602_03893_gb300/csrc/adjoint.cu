@@ -212,7 +212,8 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
         const PairRef* refs = refs2[cur];
         if (valid) {
             float acc = 0.f;         // FP32 over the chunk's 32 sensors, Kahan across chunks
-#pragma unroll 2
+            constexpr int UNROLL = P == 7 ? 4 : 2;   // 8 terms need the registers of the deeper unroll
+#pragma unroll UNROLL
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
                 float invR, phi;
