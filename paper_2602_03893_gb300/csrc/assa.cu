@@ -38,6 +38,18 @@ constexpr size_t ASSA_HDR = (sizeof(AssaSmem) + 127) & ~(size_t)127;
 // Impulse band of one (slab, sensor) on the fine grid: samples alpha w - K .. alpha (w + LB - 1) + K.
 __host__ __device__ __forceinline__ int assa_zb(int LB, int alpha, int K) { return (alpha * LB + 2 * K + 3) & ~3; }
 
+// Snapping by the float representation: for |x| < 2^22, x + 1.5 * 2^23 rounds to the nearest
+// integer in the float's mantissa, so its bits minus SNAP_BITS are that integer: round(x), which is
+// floor(x + 1/2) except at exact ties (rounded to even there; the oracle bounds tie decisions).
+constexpr float SNAP_MAGIC = 12582912.f;           // 1.5 * 2^23
+constexpr unsigned SNAP_BITS = 0x4B400000u;         // its bits
+
+// Snapped fine sample of a pair, alpha n0 + round(phi alpha / Delta): base = alpha n0 - SNAP_BITS
+// (wrapping).
+__device__ __forceinline__ int assa_snap(float phi, float aInvD, unsigned base) {
+    return (int)((unsigned)__float_as_int(fmaf(phi, aInvD, SNAP_MAGIC)) + base);
+}
+
 // alpha n0, clamped far outside any record (the snapped sample then fails the range tests).
 __device__ __forceinline__ int assa_an0(int alpha, int n0) {
     const long long an = (long long)alpha * n0;
@@ -158,7 +170,7 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
             r.R0 = __shfl_sync(0xffffffffu, refs.R0, src);
             r.phi0 = __shfl_sync(0xffffffffu, refs.phi0, src);
             r.n0 = __shfl_sync(0xffffffffu, refs.n0, src);
-            const int an0 = assa_an0(alpha, r.n0);
+            const unsigned base = (unsigned)assa_an0(alpha, r.n0) - SNAP_BITS;
             const float ax = ox * (2.f * r.v0x + ox);
             const float ay0 = oy0 * (2.f * r.v0y + oy0), ay1 = oy1 * (2.f * r.v0y + oy1);
 #pragma unroll
@@ -169,7 +181,7 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
                 float invR, phi;
                 pair_phase_num(r, num, invR, phi);
                 // snapped fine sample: floor((R / v - t0) alpha fs + 1/2) = alpha n0 + floor(phi alpha / Delta + 1/2)
-                const int k = an0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
+                const int k = assa_snap(phi, aInvD, base);
                 const int kb = k - kb0;
                 if (Ai != 0.f && k >= 0 && k < Nup && kb >= 0 && kb < ZB) atomicAdd(&zb[kb], Ai * invR);
             }
@@ -262,7 +274,7 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
     // the shared references carry alpha n0 (clamped) and the sensor's row j alpha Nt of dconv
     auto ref_fine = [&](int j) {
         const PairRef r = make_ref(c0x, c0y, c0z, a.xyz[3 * j], a.xyz[3 * j + 1], a.xyz[3 * j + 2], a);
-        return adj_ref(r, assa_an0(alpha, r.n0), j * Nup);
+        return adj_ref(r, (int)((unsigned)assa_an0(alpha, r.n0) - SNAP_BITS), j * Nup);   // see assa_snap
     };
     KahanF kA;                       // across chunks; FP32 within a chunk of 32 sensors
     if (warp == LASTW && lane < min(ASSA_ADJ_SC, a.Nd)) refs2[0][lane] = ref_fine(lane);
@@ -279,7 +291,7 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
                 const AdjRef r = refs[q];
                 float invR, phi;
                 pair_phase_r(r, dx, dy, dz, d2, invR, phi);
-                const int k = r.n0 + (int)floorf(fmaf(phi, aInvD, 0.5f));
+                const int k = assa_snap(phi, aInvD, (unsigned)r.n0);
                 if ((unsigned)k < (unsigned)Nup) acc = fmaf(__ldg(dconv + (size_t)(unsigned)(r.row + k)), invR, acc);
             }
             kA.add(acc);
