@@ -17,6 +17,7 @@ sharded, on one-GPU machines): value = max-over-ranks time / (K * N).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -374,14 +375,29 @@ def main():
             a1.record(stream)
             torch.cuda.synchronize()
             times[name] = max_over_ranks(a0.elapsed_time(a1) / args.steps, world)
+        # one whole IR iteration (Algorithm 2, same rule and data) with ASSA as the solver's operator
+        sa = _lib.Solver(gs, arr, dataclasses.replace(params, op=_lib.OP_ASSA, n_min=ASSA_NMIN))
+        for _ in range(2):
+            sa.gpair_step(b, want_loss=False)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            sa.gpair_step(b, want_loss=False)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        times["ir_step"] = max_over_ranks(a0.elapsed_time(a1) / args.steps, world)
+        sa.close()
         assert _lib.gpair_last_device_status() == 0
         nh = math.ceil(3.0 * float(np.float32(g.sigma)) / (float(np.float32(w.v)) / float(np.float32(w.fs))))
         alpha = max(1, math.ceil(((ASSA_NMIN - 1) / 2.0) / nh))
         assa = {"n_min": ASSA_NMIN, "alpha": alpha, "n_half": nh, "forward_ms": times["forward"],
                 "adjoint_ms": times["adjoint"], "fwd_plus_adj_ms": times["forward"] + times["adjoint"],
+                "ir_step_ms": times["ir_step"],
                 "pair_evals_per_s": 2 * pairs_of(w) / ((times["forward"] + times["adjoint"]) / 1e3),
                 "paper_ms": {"forward": 37.41, "adjoint": 4.99, "hardware": "RTX 5090 (the paper's)"},
-                "includes": "forward: slab info + kernel + slab reduction; adjoint: correlated residual + kernel"}
+                "includes": "forward: slab info + kernel + slab reduction; adjoint: correlated residual + kernel; "
+                            "ir_step: gpair_step with op = ASSA (NPC, forward, FP64 loss, adjoint, Adam)"}
 
     # ---- the vessel continuity regulariser (value + gradient) on the same image, HBM-bound
     vcr = None

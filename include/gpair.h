@@ -155,6 +155,11 @@ typedef struct {
     /* Vessel continuity regulariser (Methods: loss = data + lambda (R_H + beta R_TV), Algorithm 2);
      * vcr_lambda = 0 disables it.  Grid Gaussians and the Adam rule only; see gpair_vcr. */
     float vcr_lambda, vcr_beta, vcr_eps;
+    /* Operator of every forward and adjoint in the step: 0 = the windowed closed form of
+     * gpair_forward / gpair_adjoint (the default); 1 = the paper's discretised operator with
+     * adaptive supersampling alignment (Algorithm 1, gpair_assa_forward / gpair_assa_adjoint;
+     * grid Gaussians only) at the minimum pulse length n_min (the paper's is 25; ignored for 0). */
+    int op, n_min;
 } gpair_step_params;
 
 typedef struct gpair_solver gpair_solver;
@@ -185,8 +190,8 @@ gpair_status gpair_solver_set_state(gpair_solver* s, const float* z, const float
                                     int t, void* stream);
 
 /* Device-side timing of gpair_step (tracing).  enable != 0: every following step records CUDA
- * events on its own stream around the forward slab kernel, the adjoint kernel and the whole
- * step.  gpair_solver_timings synchronises on the last recorded event, writes the summed
+ * events on its own stream around the forward slab kernel (ASSA: the band kernel), the adjoint
+ * kernel (ASSA: the gather kernel) and the whole step.  gpair_solver_timings synchronises on the last recorded event, writes the summed
  * milliseconds ms[0] = forward slab kernel, ms[1] = adjoint kernel, ms[2] = whole step and the
  * number of recorded steps (may be NULL), and clears the record. */
 gpair_status gpair_solver_profile(gpair_solver* s, int enable);

@@ -266,3 +266,39 @@ def ir(g: Gaussians, sensors, v, fs, t0, Nt, b, iters, k=3.0, rule="adam", npc=T
                int(T0 if T0 is not None else iters), float(Tmult), float(b1), float(b2),
                float(adam_eps), _p(x), _p(loss), _p(resid))
     return x, loss, resid
+
+
+def ir_assa(g: Gaussians, sigma, sensors, v, fs, t0, Nt, b, iters, n_min=25, rule="adam", npc=True,
+            npc_eps=1e-8, eta_max=1e-2, eta_min=0.0, T0=None, Tmult=1.0, b1=0.9, b2=0.999, adam_eps=1e-8):
+    """Algorithm 2 on amplitudes with the paper's discretised operator (Algorithm 1) as F and F^T:
+    the same iteration as `ir` (NPC x = (z + eps)^2, L = |F x - b|^2 / N, exact gradient
+    F^T (2 (y - b) / N) chained through NPC, CAWR step size, Adam; or steepest descent with the
+    exact line search alpha = <r, F g> / |F g|^2), for Gaussians sharing the width sigma.
+    Returns (x*, loss[iters], resid[iters]) for the iterate entering each iteration."""
+    s = _d(sensors).reshape(-1, 3)
+    Nd = s.shape[0]
+    bb = _d(b).reshape(Nd, Nt)
+    N = float(Nd * Nt)
+    z, m, vv = np.zeros(g.M), np.zeros(g.M), np.zeros(g.M)
+    loss, resid = np.zeros(iters), np.zeros(iters)
+    F = lambda x: assa_forward(Gaussians(g.c, g.sigma, x), sigma, s, v, fs, t0, Nt, n_min=n_min)
+    Ft = lambda d: assa_adjoint(g, sigma, s, v, fs, t0, Nt, d, n_min=n_min)
+    T0 = T0 if T0 is not None else iters
+    for t in range(iters):
+        x = (z + npc_eps) ** 2 if (npc and rule == "adam") else z.copy()
+        r = F(x) - bb
+        ss = float(np.sum(r * r))
+        loss[t], resid[t] = ss / N, np.sqrt(ss)
+        if rule == "adam":
+            gz = Ft(2.0 * r / N)
+            if npc:
+                gz = gz * 2.0 * (z + npc_eps)
+            adam(z, m, vv, np.ascontiguousarray(gz), t + 1, cawr(t, eta_max, eta_min, T0, Tmult), b1, b2,
+                 adam_eps)
+        else:
+            gg = Ft(r)
+            Fg = F(gg)
+            den = float(np.sum(Fg * Fg))
+            z -= (float(np.sum(r * Fg)) / den if den > 0.0 else 0.0) * gg
+    x = (z + npc_eps) ** 2 if (npc and rule == "adam") else z
+    return x, loss, resid

@@ -21,6 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device mem
           7: "problem exceeds the fixed scratch of the allocation-free entry point"}
 
 RULE_ADAM, RULE_GD_LINESEARCH = 0, 1
+OP_EXACT, OP_ASSA = 0, 1          # gpair_step_params.op
 
 # Symbols declared in include/gpair.h (checked by the CPU test suite).
 EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
@@ -55,7 +56,7 @@ class _Array(ctypes.Structure):
 class _StepParams(ctypes.Structure):
     _fields_ = [("rule", c_int), ("npc", c_int), ("npc_eps", c_float), ("eta_max", c_float), ("eta_min", c_float),
                 ("T0", c_int), ("T_mult", c_float), ("beta1", c_float), ("beta2", c_float), ("adam_eps", c_float),
-                ("vcr_lambda", c_float), ("vcr_beta", c_float), ("vcr_eps", c_float)]
+                ("vcr_lambda", c_float), ("vcr_beta", c_float), ("vcr_eps", c_float), ("op", c_int), ("n_min", c_int)]
 
 
 _lib = None
@@ -329,10 +330,13 @@ class StepParams:
     vcr_lambda: float = 0.0      # vessel continuity regulariser weight (0: off)
     vcr_beta: float = 0.0        # TV share of the regulariser
     vcr_eps: float = 1e-8
+    op: int = OP_EXACT           # operator of the step's forwards and adjoints
+    n_min: int = 25              # ASSA minimum pulse length (op = OP_ASSA)
 
     def _c(self) -> _StepParams:
         return _StepParams(self.rule, self.npc, self.npc_eps, self.eta_max, self.eta_min, self.T0, self.T_mult,
-                           self.beta1, self.beta2, self.adam_eps, self.vcr_lambda, self.vcr_beta, self.vcr_eps)
+                           self.beta1, self.beta2, self.adam_eps, self.vcr_lambda, self.vcr_beta, self.vcr_eps,
+                           self.op, self.n_min)
 
 
 class Solver:

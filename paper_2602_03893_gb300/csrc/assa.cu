@@ -306,29 +306,36 @@ size_t assa_fwd_smem(int LB, const AssaTable& T) {
     return ASSA_HDR + (size_t)ASSA_SPC * assa_zb(LB, T.alpha, T.K) * sizeof(float);
 }
 
+// ev (optional): two events recorded immediately before and after the main kernel.
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
-                                cudaStream_t st) {
+                                const cudaEvent_t* ev, cudaStream_t st) {
     static const CUtensorMap zero_map = [] { CUtensorMap z; memset(&z, 0, sizeof(z)); return z; }();
     const size_t smem = assa_fwd_smem(LB, T);
     cudaError_t e = cudaFuncSetAttribute(assa_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.Nd + ASSA_SPC - 1) / ASSA_SPC, S);
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     assa_fwd_kernel<<<grid, ASSA_THREADS, smem, st>>>(g, a, si, partial, rows, LB, status, tmap != nullptr,
                                                       tmap ? *tmap : zero_map, T);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+    return e;
 }
 
 size_t assa_dconv_bytes(const ArrDev& a, const AssaTable& T) { return (size_t)a.Nd * T.alpha * a.Nt * sizeof(float); }
 
 cudaError_t launch_assa_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, const AssaTable& T,
-                                float* dconv, cudaStream_t st) {
+                                float* dconv, const cudaEvent_t* ev, cudaStream_t st) {
     dim3 dgrid((T.alpha * a.Nt + 255) / 256, a.Nd);
     assa_dconv_kernel<<<dgrid, 256, assa_dconv_smem(T), st>>>(delta, a.Nt, T, dconv);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     assa_adj_kernel<<<(unsigned)g.ntiles, TILE, 0, st>>>(g, a, dconv, T, gA);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+    return e;
 }
 
 }  // namespace gp

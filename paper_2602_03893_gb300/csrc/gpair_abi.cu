@@ -38,10 +38,10 @@ cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float
                        double* partial, double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
-                                cudaStream_t st);
+                                const cudaEvent_t* ev, cudaStream_t st);
 size_t assa_dconv_bytes(const ArrDev& a, const AssaTable& T);
 cudaError_t launch_assa_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, const AssaTable& T,
-                                float* dconv, cudaStream_t st);
+                                float* dconv, const cudaEvent_t* ev, cudaStream_t st);
 cudaError_t launch_resid(const float* y, const float* b, float* delta, float scale, int64_t n, double* partial,
                          double* out, cudaStream_t st);
 cudaError_t launch_reduce2(const float* a, const float* b, const float* c, int64_t n, double* partial, double* out,
@@ -577,21 +577,16 @@ gpair_status assa_inputs(const gpair_gaussians* gi, const gpair_array* ai, int n
     return GPAIR_OK;
 }
 
-gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai, int n_min, float* y, void* stream) {
-    GaussDev g;
-    ArrDev a;
-    AssaTable T;
-    gpair_status s = assa_inputs(gi, ai, n_min, g, a, T);
-    if (s != GPAIR_OK) return s;
-    if (!y) return GPAIR_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the slab bands must hold the pulse half-width N_half v / fs plus half a fine step of snapping
+// The slab bands of the ASSA forward hold the pulse half-width N_half v / fs plus half a fine step.
+ArrDev assa_band_array(const GaussDev& g, const ArrDev& a, const AssaTable& T) {
     ArrDev aa = a;
     aa.k = (float)((T.n_half * (double)a.Delta + 0.5 * (double)a.Delta / T.alpha) / (double)g.sigma * 1.001 + 1e-3);
-    FwdPlan p = plan_forward(g, aa);
-    void* scratch = nullptr;
-    int* status = nullptr;
-    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    return aa;
+}
+
+// ASSA forward into y with scratch of p.bytes (p = plan_forward(g, assa_band_array(...))).
+gpair_status run_assa_forward(const GaussDev& g, const ArrDev& aa, const AssaTable& T, const FwdPlan& p, float* y,
+                              void* scratch, int* status, const cudaEvent_t* ev, cudaStream_t st) {
     char* base = static_cast<char*>(scratch);
     SlabInfo* si = reinterpret_cast<SlabInfo*>(base + p.off_si);
     int2* rows = reinterpret_cast<int2*>(base + p.off_rows);
@@ -600,9 +595,26 @@ gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai
     memset(&map, 0, sizeof(map));
     const bool tma = make_tmap(g, &map);
     cudaError_t e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
-    if (e == cudaSuccess) e = launch_assa_forward(g, aa, si, p.S, part, rows, p.LB, status, tma ? &map : nullptr, T, st);
+    if (e == cudaSuccess)
+        e = launch_assa_forward(g, aa, si, p.S, part, rows, p.LB, status, tma ? &map : nullptr, T, ev, st);
     if (e == cudaSuccess) e = launch_slab_reduce(g, aa, part, rows, p.S, p.PL, y, st);
     return cuda_status(e);
+}
+
+gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai, int n_min, float* y, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    AssaTable T;
+    gpair_status s = assa_inputs(gi, ai, n_min, g, a, T);
+    if (s != GPAIR_OK) return s;
+    if (!y) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ArrDev aa = assa_band_array(g, a, T);
+    FwdPlan p = plan_forward(g, aa);
+    void* scratch = nullptr;
+    int* status = nullptr;
+    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    return run_assa_forward(g, aa, T, p, y, scratch, status, nullptr, st);
 }
 
 gpair_status gpair_assa_adjoint(const gpair_gaussians* gi, const gpair_array* ai, int n_min, const float* delta,
@@ -616,7 +628,7 @@ gpair_status gpair_assa_adjoint(const gpair_gaussians* gi, const gpair_array* ai
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* scratch = nullptr;
     if ((s = get_scratch(st, assa_dconv_bytes(a, T), &scratch, nullptr)) != GPAIR_OK) return s;
-    return cuda_status(launch_assa_adjoint(g, a, delta, gA, T, static_cast<float*>(scratch), st));
+    return cuda_status(launch_assa_adjoint(g, a, delta, gA, T, static_cast<float*>(scratch), nullptr, st));
 }
 
 gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* grad,
@@ -718,7 +730,12 @@ struct gpair_solver {
     void* qbuf = nullptr;    // expansion table of the amplitude adjoint (grid Gaussians)
     float* vcrF = nullptr;   // regulariser fields, 9 M floats (vcr_lambda > 0)
     int* status = nullptr;
-    FwdPlan plan;
+    FwdPlan plan;            // of a, or of aa with the ASSA operator
+    // ASSA operator (op = 1): pulse table, band-widened array and the adjoint's kernel-response table.
+    bool assa = false;
+    AssaTable T;
+    ArrDev aa;
+    float* dconv = nullptr;
     // Profiling (gpair_solver_profile): per recorded step six events on the step's stream --
     // step start, forward slab kernel start/end, adjoint kernel start/end, step end.
     bool prof = false;
@@ -736,6 +753,19 @@ double cawr(int t, const gpair_step_params& p) {
         while (Tcur >= Ti) { Tcur -= Ti; Ti *= p.T_mult; }
     }
     return p.eta_min + 0.5 * (p.eta_max - p.eta_min) * (1.0 + std::cos(M_PI * Tcur / Ti));
+}
+
+// y = F(S->g with amplitudes S->g.A) on the solver's operator; ev (optional) brackets its main kernel.
+gpair_status solver_forward(gpair_solver* S, float* y, const cudaEvent_t* ev, cudaStream_t st) {
+    if (S->assa) return run_assa_forward(S->g, S->aa, S->T, S->plan, y, S->fwd_scratch, S->status, ev, st);
+    return run_forward(S->g, S->a, y, st, S->fwd_scratch, S->status, S->plan, ev);
+}
+
+// gA = F^T delta on the solver's operator.
+gpair_status solver_adjoint(gpair_solver* S, const float* delta, float* gA, const cudaEvent_t* ev, cudaStream_t st) {
+    if (S->assa) return cuda_status(launch_assa_adjoint(S->g, S->a, delta, gA, S->T, S->dconv, ev, st));
+    // the amplitude adjoint needs only the tile summaries of the forward scratch (same layout)
+    return run_adjoint(S->g, S->a, delta, gA, nullptr, nullptr, st, S->fwd_scratch, ev, S->qbuf);
 }
 }  // namespace
 
@@ -763,12 +793,23 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
         return GPAIR_ERR_INVALID_ARG;
     if (vcr && (prm->rule != GPAIR_RULE_ADAM || !g.grid || (int64_t)g.ny * g.nz > (int64_t)INT32_MAX))
         return GPAIR_ERR_UNSUPPORTED;
+    if (prm->op != 0 && prm->op != 1) return GPAIR_ERR_INVALID_ARG;
+    const bool assa = prm->op == 1;
+    if (assa && prm->n_min < 1) return GPAIR_ERR_INVALID_ARG;
+    if (assa && !g.grid) return GPAIR_ERR_UNSUPPORTED;
     gpair_solver* S = new gpair_solver();
     S->g = g;
     S->a = a;
     S->p = *prm;
+    S->assa = assa;
+    if (assa && !make_assa_table(g, a, prm->n_min, S->T)) {
+        delete S;
+        return GPAIR_ERR_UNSUPPORTED;
+    }
     const size_t M = (size_t)g.M, N = (size_t)a.Nd * a.Nt;
-    S->plan = plan_forward(g, a);
+    if (assa) S->aa = assa_band_array(g, a, S->T);
+    S->plan = plan_forward(g, assa ? S->aa : a);
+    const size_t qbytes = assa ? 0 : adjoint_q_bytes(g, a);
     bool ok = cudaMalloc(&S->z, M * 4) == cudaSuccess && cudaMalloc(&S->m, M * 4) == cudaSuccess &&
               cudaMalloc(&S->v, M * 4) == cudaSuccess && cudaMalloc(&S->x, M * 4) == cudaSuccess &&
               cudaMalloc(&S->gx, M * 4) == cudaSuccess && cudaMalloc(&S->y, N * 4) == cudaSuccess &&
@@ -776,7 +817,8 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               (prm->rule != GPAIR_RULE_GD_LINESEARCH || cudaMalloc(&S->Fg, N * 4) == cudaSuccess) &&
               cudaMalloc(&S->red, sizeof(double) * (2 * red_blocks() + 8)) == cudaSuccess &&
               cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
-              (adjoint_q_bytes(g, a) == 0 || cudaMalloc(&S->qbuf, adjoint_q_bytes(g, a)) == cudaSuccess) &&
+              (qbytes == 0 || cudaMalloc(&S->qbuf, qbytes) == cudaSuccess) &&
+              (!assa || cudaMalloc(&S->dconv, assa_dconv_bytes(a, S->T)) == cudaSuccess) &&
               cudaMalloc(&S->status, sizeof(int)) == cudaSuccess &&
               (!vcr || cudaMalloc(&S->vcrF, M * 9 * sizeof(float)) == cudaSuccess);
     if (!ok) {
@@ -801,7 +843,7 @@ void gpair_solver_destroy(gpair_solver* S) {
     if (!S) return;
     cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
     cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
-    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->vcrF);
+    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->vcrF); cudaFree(S->dconv);
     for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
     delete S;
 }
@@ -838,7 +880,6 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
     double* res = S->red + 2 * red_blocks();
     cudaError_t e;
     gpair_status s;
-    void* adj_scratch = S->fwd_scratch;   // the adjoint needs only the tile summaries (same layout)
     const cudaEvent_t* ev = nullptr;
     if (S->prof) {
         while ((int)S->evs.size() < 6 * (S->nrec + 1)) {
@@ -852,13 +893,10 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
     if (S->p.rule == GPAIR_RULE_ADAM) {
         const int npc = S->p.npc != 0;
         if ((e = launch_npc(S->z, S->x, M, npc, S->p.npc_eps, st)) != cudaSuccess) return cuda_status(e);
-        if ((s = run_forward(S->g, S->a, S->y, st, S->fwd_scratch, S->status, S->plan, ev ? ev + 1 : nullptr)) != GPAIR_OK)
-            return s;
+        if ((s = solver_forward(S, S->y, ev ? ev + 1 : nullptr, st)) != GPAIR_OK) return s;
         if ((e = launch_resid(S->y, b, S->delta, (float)(2.0 / (double)N), N, partial, res, st)) != cudaSuccess)
             return cuda_status(e);
-        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr, S->qbuf)) !=
-            GPAIR_OK)
-            return s;
+        if ((s = solver_adjoint(S, S->delta, S->gx, ev ? ev + 3 : nullptr, st)) != GPAIR_OK) return s;
         if (S->vcrF &&   // grad_x += lambda grad R_VCR(x); R_VCR(x) into res[4]
             (e = launch_vcr(S->x, S->g.nx, S->g.ny, S->g.nz, S->p.vcr_beta, S->p.vcr_eps, S->p.vcr_lambda, S->vcrF,
                             partial, res + 4, S->gx, st)) != cudaSuccess)
@@ -872,14 +910,11 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
     } else {
         // steepest descent on x = z with the exact line search alpha = <r, F g> / |F g|^2
         S->g.A = S->z;
-        if ((s = run_forward(S->g, S->a, S->y, st, S->fwd_scratch, S->status, S->plan, ev ? ev + 1 : nullptr)) != GPAIR_OK)
-            return s;
+        if ((s = solver_forward(S, S->y, ev ? ev + 1 : nullptr, st)) != GPAIR_OK) return s;
         if ((e = launch_resid(S->y, b, S->delta, 1.0f, N, partial, res, st)) != cudaSuccess) return cuda_status(e);
-        if ((s = run_adjoint(S->g, S->a, S->delta, S->gx, nullptr, nullptr, st, adj_scratch, ev ? ev + 3 : nullptr, S->qbuf)) !=
-            GPAIR_OK)
-            return s;
+        if ((s = solver_adjoint(S, S->delta, S->gx, ev ? ev + 3 : nullptr, st)) != GPAIR_OK) return s;
         S->g.A = S->gx;
-        if ((s = run_forward(S->g, S->a, S->Fg, st, S->fwd_scratch, S->status, S->plan)) != GPAIR_OK) return s;
+        if ((s = solver_forward(S, S->Fg, nullptr, st)) != GPAIR_OK) return s;
         if ((e = launch_ls(S->delta, S->Fg, N, S->z, S->gx, M, partial, res + 2, st)) != cudaSuccess)
             return cuda_status(e);
         S->g.A = S->x;

@@ -99,6 +99,16 @@ def test_size_limits_and_new_entry_points_rejected_on_the_host(lib):
     assert lib.gpair_image_metrics(y, y, 8, 8, 5, 7, 1.0, out, None) == 5                      # z shorter than it
     lib.gpair_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_void_p]
     assert lib.gpair_wait_selftest(0, None) == 1
+    # solver operator choice: op outside {0, 1}, n_min < 1 and free centres with ASSA
+    lib.gpair_solver_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    prm = _lib.StepParams(op=2)._c()
+    assert lib.gpair_solver_create(ctypes.byref(g), ctypes.byref(a), ctypes.byref(prm), ctypes.byref(h)) == 1
+    prm = _lib.StepParams(op=_lib.OP_ASSA, n_min=0)._c()
+    assert lib.gpair_solver_create(ctypes.byref(g), ctypes.byref(a), ctypes.byref(prm), ctypes.byref(h)) == 1
+    prm = _lib.StepParams(op=_lib.OP_ASSA)._c()
+    assert lib.gpair_solver_create(ctypes.byref(soa), ctypes.byref(a), ctypes.byref(prm), ctypes.byref(h)) == 5
+    assert not h
 
 
 def test_product_package_never_imports_the_oracle():

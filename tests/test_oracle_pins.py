@@ -390,6 +390,52 @@ def test_assa_adjoint_identity():
     assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Fx) * np.linalg.norm(delta)
 
 
+def _assa_dense_problem():
+    g = synth.centred_grid(4, 4, 4, 0.2e-3)
+    G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, np.zeros(g.M))
+    sens = synth.cap_sensors(6, 5e-3, 180.0)
+    v, fs, t0, Nt = 1500.0, 40e6, 0.0, 256
+    F = np.stack([oracle.assa_forward(oracle.Gaussians(G.c, G.sigma, np.eye(g.M)[i]), g.sigma, sens, v, fs, t0,
+                                      Nt).ravel() for i in range(g.M)], 1)
+    b = F @ np.random.default_rng(22).uniform(0, 1, g.M)
+    return g, G, sens, v, fs, t0, Nt, F, b
+
+
+def test_ir_on_assa_matches_torch_autograd():
+    """Algorithm 2 with the discretised operator (NPC, Adam, CAWR) against torch autograd and
+    torch.optim on the dense matrix of Algorithm 1's forward."""
+    torch = pytest.importorskip("torch")
+    g, G, sens, v, fs, t0, Nt, F, b = _assa_dense_problem()
+    iters, eta, T0 = 12, 0.05, 5
+    x, loss, resid = oracle.ir_assa(G, g.sigma, sens, v, fs, t0, Nt, b, iters, eta_max=eta, eta_min=0.001, T0=T0)
+    Ft, bt = torch.tensor(F), torch.tensor(b)
+    z = torch.zeros(G.M, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([z], lr=eta, betas=(0.9, 0.999), eps=1e-8)
+    sch = torch.optim.lr_scheduler.CosineAnnealingWarmRestarts(opt, T_0=T0, T_mult=1, eta_min=0.001)
+    tl = []
+    for _ in range(iters):
+        opt.zero_grad()
+        L = torch.mean((Ft @ (z + 1e-8) ** 2 - bt) ** 2)
+        tl.append(float(L))
+        L.backward()
+        opt.step()
+        sch.step()
+    xt = ((z + 1e-8) ** 2).detach().numpy()
+    assert np.allclose(loss, tl, rtol=1e-9, atol=0)
+    assert np.max(np.abs(x - xt)) <= 1e-9 * np.max(np.abs(xt))
+    assert loss[-1] < loss[0]
+
+
+def test_ir_on_assa_line_search_is_exact_minimiser():
+    g, G, sens, v, fs, t0, Nt, F, b = _assa_dense_problem()
+    x1, loss, _ = oracle.ir_assa(G, g.sigma, sens, v, fs, t0, Nt, b, 1, rule="linesearch", npc=False)
+    gr = F.T @ -b
+    alpha = -float(b @ (F @ gr)) / float(np.sum((F @ gr) ** 2))   # argmin_a |F(-a g) - b|^2, g = F^T (0 - b)
+    assert np.allclose(x1, -alpha * gr, rtol=1e-10, atol=0)
+    _, loss2, _ = oracle.ir_assa(G, g.sigma, sens, v, fs, t0, Nt, b, 3, rule="linesearch", npc=False)
+    assert np.all(np.diff(loss2) < 0)
+
+
 def test_assa_stages_equal_the_folded_single_sum():
     """Projection, transposed convolution and decimation collapse to
     y_j[n] = sum_i (x_i / r_ij) h[alpha n - k_ij] over |alpha n - k_ij| <= K; evaluated here pair by

@@ -61,6 +61,48 @@ def test_line_search_matches_oracle(problem):
     assert rel_l2(x, xo) < 1e-3
 
 
+def test_adam_on_assa_operator_matches_oracle(problem):
+    """gpair_step with the discretised operator (op = ASSA, Algorithm 1) against the oracle's
+    Algorithm 2 built on its own ASSA forward and adjoint."""
+    w, G, b = problem
+    iters, eta = 20, 0.05
+    p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, npc_eps=1e-8, eta_max=eta, eta_min=0.0, T0=iters,
+                        T_mult=1.0, adam_eps=1e-20, op=_lib.OP_ASSA, n_min=25)
+    x, loss, resid = _gpu_ir(w, b, iters, p)
+    xo, lo, ro = oracle.ir_assa(G, G.sigma[0], w.sensors, w.v, w.fs, w.t0, w.Nt, b, iters, n_min=25, rule="adam",
+                                npc=True, npc_eps=1e-8, eta_max=eta, eta_min=0.0, T0=iters, adam_eps=1e-20)
+    print("loss gpu", loss[[0, 5, 10, 19]], "oracle", lo[[0, 5, 10, 19]], "x rel", rel_l2(x, xo))
+    assert loss[-1] < loss[0]
+    assert abs(loss[0] - lo[0]) <= 1e-6 * lo[0]
+    assert np.max(np.abs(loss - lo) / lo) < 2e-3
+    assert rel_l2(x, xo) < 2e-3
+
+
+def test_line_search_on_assa_operator_matches_oracle(problem):
+    w, G, b = problem
+    iters = 8
+    p = _lib.StepParams(rule=_lib.RULE_GD_LINESEARCH, npc=0, op=_lib.OP_ASSA, n_min=25)
+    x, loss, resid = _gpu_ir(w, b, iters, p)
+    xo, lo, ro = oracle.ir_assa(G, G.sigma[0], w.sensors, w.v, w.fs, w.t0, w.Nt, b, iters, n_min=25,
+                                rule="linesearch", npc=False)
+    assert np.all(np.diff(loss) < 0)
+    assert np.max(np.abs(resid - ro) / ro) < 1e-4
+    assert rel_l2(x, xo) < 1e-3
+
+
+def test_assa_solver_profile_records_its_kernels(problem):
+    w, G, b = problem
+    gs, arr = device_inputs(w)
+    s = _lib.Solver(gs, arr, _lib.StepParams(op=_lib.OP_ASSA))
+    bt = torch.as_tensor(b, device="cuda")
+    s.gpair_solver_profile(True)
+    for _ in range(3):
+        s.gpair_step(bt, want_loss=False)
+    ms, n = s.gpair_solver_timings()
+    s.close()
+    assert n == 3 and ms[0] > 0 and ms[1] > 0 and ms[2] >= ms[0] + ms[1]
+
+
 def test_checkpoint_resume(problem):
     w, G, b = problem
     p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, eta_max=0.02, T0=20, adam_eps=1e-20)
