@@ -421,6 +421,11 @@ def main():
                "peak_GBs": HBM_GBS, "frac": vbytes / (vms / 1e3) / 1e9 / HBM_GBS,
                "includes": "fields + FP64 block partials + transposed-stencil gradient (no host sync)"}
 
+    # the two pipes' rates measured on this device right after the timed work (FFMA and ex2 chains)
+    pipe_peaks = {"fp32": _lib.gpair_pipe_peak(_lib.PIPE_FP32) / 1e12, "mufu": _lib.gpair_pipe_peak(_lib.PIPE_MUFU) / 1e12,
+                  "unit": "T lane-ops/s", "method": "gpair_pipe_peak: 8 dependent-chain FFMA / ex2.approx streams per "
+                                                     "thread, 8 CTAs x 256 threads per SM, CUDA events"}
+
     clocks = sampler.summary()
     pairs, samples = work_units(w)
     fwd_avg = fwd_ms / max(nrec, 1) / 1e3
@@ -434,9 +439,11 @@ def main():
         t_fp32, t_mufu = F / p_fp32, X / p_mufu
         pipe = "fp32" if t_fp32 >= t_mufu else "mufu"
         ops, peak = (F, p_fp32) if pipe == "fp32" else (X, p_mufu)
+        pm = pipe_peaks[pipe] * 1e12
         kern[op] = {"kernel": names[op], "s_per_launch": t, "bound_pipe": pipe, "t_bound_s": max(t_fp32, t_mufu),
                     "alg_fp32_ops": F, "alg_mufu_ops": X, "achieved": ops / t / 1e12, "peak": peak / 1e12,
-                    "frac": ops / t / peak}
+                    "frac": ops / t / peak, "peak_measured": pm / 1e12, "frac_of_measured": ops / t / pm,
+                    "t_bound_measured_s": max(F / (pipe_peaks["fp32"] * 1e12), X / (pipe_peaks["mufu"] * 1e12))}
     dom = "forward" if fwd_avg >= adj_avg else "adjoint"
     src = src_hash("forward.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
     tr = profiled_traffic(kern[dom]["kernel"], src)
@@ -450,6 +457,9 @@ def main():
     # both operators of the iteration together: their bounds over their measured times
     roofline["fwd_plus_adj_frac"] = ((kern["forward"]["t_bound_s"] + kern["adjoint"]["t_bound_s"]) /
                                      (fwd_avg + adj_avg))
+    roofline["fwd_plus_adj_frac_of_measured"] = ((kern["forward"]["t_bound_measured_s"] +
+                                                  kern["adjoint"]["t_bound_measured_s"]) / (fwd_avg + adj_avg))
+    roofline["pipe_peaks_measured"] = pipe_peaks
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = kd["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
 

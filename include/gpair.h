@@ -265,6 +265,16 @@ gpair_status gpair_image_metrics(const float* x, const float* ref, int nx, int n
  * in the stream's device status word and returns normally, leaving the context usable.  The next
  * gpair_last_device_status(stream) returns GPAIR_ERR_TIMEOUT.  The paper has no counterpart. */
 gpair_status gpair_wait_selftest(int polls, void* stream);
+
+/* gpair_pipe_peak -- measured throughput of a pipe that bounds the operators, for their roofline
+ * (the operators are FP32/MUFU instruction work, not a contraction and not HBM traffic).
+ * pipe GPAIR_PIPE_FP32: fused multiply-adds (fmaf), GPAIR_PIPE_MUFU: ex2.approx; each thread runs
+ * 8 independent dependency chains, 8 CTAs of 256 threads per SM.  One warm-up launch, then `reps`
+ * (1..1000) launches timed with CUDA events on `stream`; writes lane operations per second to
+ * *lane_ops_per_s (host).  Synchronises `stream`; allocates and frees a small device buffer.
+ * Errors: GPAIR_ERR_INVALID_ARG for an unknown pipe, reps outside 1..1000 or a NULL output. */
+typedef enum { GPAIR_PIPE_FP32 = 0, GPAIR_PIPE_MUFU = 1 } gpair_pipe;
+gpair_status gpair_pipe_peak(int pipe, int reps, double* lane_ops_per_s, void* stream);
 /* Library version string. */
 const char* gpair_version(void);
 

@@ -29,7 +29,7 @@ EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_vox
            "gpair_solver_profile", "gpair_solver_timings",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
            "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_vcr", "gpair_zmap",
-           "gpair_image_metrics", "gpair_version")
+           "gpair_image_metrics", "gpair_pipe_peak", "gpair_version")
 
 
 class GpairError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         lib.gpair_release_scratch.argtypes = []
         lib.gpair_release_scratch.restype = None
         lib.gpair_wait_selftest.argtypes = [c_int, P]
+        lib.gpair_pipe_peak.argtypes = [c_int, c_int, ctypes.POINTER(c_double), P]
         lib.gpair_assa_forward.argtypes = [P, P, c_int, P, P]
         lib.gpair_zmap.argtypes = [P, c_int, c_int, c_int, P, P]
         lib.gpair_image_metrics.argtypes = [P, P, c_int, c_int, c_int, c_int, c_float, ctypes.POINTER(c_double), P]
@@ -305,6 +306,17 @@ def gpair_wait_selftest(polls: int, stream=None) -> None:
     """Launch the bounded-wait self-test (a wait nothing completes, given up after `polls` polls);
     the next gpair_last_device_status reports the timeout."""
     _check("gpair_wait_selftest", load().gpair_wait_selftest(int(polls), _stream(stream)))
+
+
+PIPE_FP32, PIPE_MUFU = 0, 1
+
+
+def gpair_pipe_peak(pipe: int, reps: int = 5, stream=None) -> float:
+    """Measured lane operations per second of the FP32 FMA (PIPE_FP32) or MUFU ex2 (PIPE_MUFU)
+    pipe on the current device."""
+    out = c_double()
+    _check("gpair_pipe_peak", load().gpair_pipe_peak(int(pipe), int(reps), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def gpair_version() -> str:

@@ -109,6 +109,11 @@ def test_size_limits_and_new_entry_points_rejected_on_the_host(lib):
     prm = _lib.StepParams(op=_lib.OP_ASSA)._c()
     assert lib.gpair_solver_create(ctypes.byref(soa), ctypes.byref(a), ctypes.byref(prm), ctypes.byref(h)) == 5
     assert not h
+    lib.gpair_pipe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    rate = ctypes.c_double()
+    assert lib.gpair_pipe_peak(2, 5, ctypes.byref(rate), None) == 1                            # unknown pipe
+    assert lib.gpair_pipe_peak(0, 0, ctypes.byref(rate), None) == 1                            # reps < 1
+    assert lib.gpair_pipe_peak(0, 5, None, None) == 1
 
 
 def test_product_package_never_imports_the_oracle():

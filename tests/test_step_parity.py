@@ -158,3 +158,4 @@ def test_bounded_wait_times_out_and_context_survives():
     assert np.abs(gpu_forward(w)).max() > 0
     with pytest.raises(_lib.GpairError):
         _lib.gpair_wait_selftest(0)                         # rejected on the host, nothing launched
+
