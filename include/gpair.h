@@ -218,7 +218,9 @@ void gpair_release_scratch(void);
  * (p != q) the four-point central mixed difference / 4 (counted for (p,q) and (q,p)), with Neumann
  * boundaries (neighbour indices clamped) and unit voxel spacing.  value_out (host, may be NULL):
  * R_VCR in FP64 (the call then synchronises `stream`); grad (device [M], may be NULL):
- * grad += lam * dR_VCR/dx.  Scratch: 9 M floats from the library's per-stream pool.  Errors:
+ * grad += lam * dR_VCR/dx.  One fused pass: the difference fields stay in shared memory, so only x
+ * and grad cross device memory; scratch is a few KB of FP64 block partials from the library's
+ * per-stream pool.  Errors:
  * GPAIR_ERR_INVALID_ARG for a NULL x, non-positive sizes or eps < 0; GPAIR_ERR_UNSUPPORTED when
  * ny nz >= 2^31. */
 gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* grad,

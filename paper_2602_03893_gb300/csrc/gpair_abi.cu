@@ -34,8 +34,8 @@ cudaError_t launch_zmap(const float* vol, int nx, int ny, int nz, float* out, cu
 size_t ssim_scratch_bytes(int64_t M);
 cudaError_t launch_ssim_sum(const float* x, const float* y, int nx, int ny, int nz, int win, float range, void* scratch,
                             double* out, cudaStream_t st);
-cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* F,
-                       double* partial, double* value_out, float* g, cudaStream_t st);
+cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, double* partial,
+                       double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
                                 const cudaEvent_t* ev, cudaStream_t st);
@@ -637,15 +637,12 @@ gpair_status gpair_vcr(const float* x, int nx, int ny, int nz, float beta, float
         return GPAIR_ERR_INVALID_ARG;
     if ((int64_t)ny * nz > (int64_t)INT32_MAX) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t M = (int64_t)nx * ny * nz;
-    const size_t fbytes = align256((size_t)M * 9 * sizeof(float));
     void* scratch = nullptr;
-    gpair_status s = get_scratch(st, fbytes + sizeof(double) * ((size_t)red_blocks() + 1), &scratch, nullptr);
+    gpair_status s = get_scratch(st, sizeof(double) * ((size_t)red_blocks() + 1), &scratch, nullptr);
     if (s != GPAIR_OK) return s;
-    float* F = static_cast<float*>(scratch);
-    double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + fbytes);
+    double* partial = static_cast<double*>(scratch);
     double* val = partial + red_blocks();
-    cudaError_t e = launch_vcr(x, nx, ny, nz, beta, eps, lam, F, partial, value_out ? val : nullptr, grad, st);
+    cudaError_t e = launch_vcr(x, nx, ny, nz, beta, eps, lam, partial, value_out ? val : nullptr, grad, st);
     if (e != cudaSuccess) return cuda_status(e);
     if (value_out) {
         if (cudaMemcpyAsync(value_out, val, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -728,7 +725,7 @@ struct gpair_solver {
     double* red = nullptr;   // reduction partials (2 * red_blocks) + results (4)
     void* fwd_scratch = nullptr;
     void* qbuf = nullptr;    // expansion table of the amplitude adjoint (grid Gaussians)
-    float* vcrF = nullptr;   // regulariser fields, 9 M floats (vcr_lambda > 0)
+    bool vcr = false;        // vessel continuity regulariser in the step (vcr_lambda > 0)
     int* status = nullptr;
     FwdPlan plan;            // of a, or of aa with the ASSA operator
     // ASSA operator (op = 1): pulse table, band-widened array and the adjoint's kernel-response table.
@@ -802,6 +799,7 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     S->a = a;
     S->p = *prm;
     S->assa = assa;
+    S->vcr = vcr;
     if (assa && !make_assa_table(g, a, prm->n_min, S->T)) {
         delete S;
         return GPAIR_ERR_UNSUPPORTED;
@@ -819,8 +817,7 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
               (qbytes == 0 || cudaMalloc(&S->qbuf, qbytes) == cudaSuccess) &&
               (!assa || cudaMalloc(&S->dconv, assa_dconv_bytes(a, S->T)) == cudaSuccess) &&
-              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess &&
-              (!vcr || cudaMalloc(&S->vcrF, M * 9 * sizeof(float)) == cudaSuccess);
+              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         gpair_solver_destroy(S);
@@ -843,7 +840,7 @@ void gpair_solver_destroy(gpair_solver* S) {
     if (!S) return;
     cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
     cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
-    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->vcrF); cudaFree(S->dconv);
+    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->dconv);
     for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
     delete S;
 }
@@ -897,9 +894,9 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
         if ((e = launch_resid(S->y, b, S->delta, (float)(2.0 / (double)N), N, partial, res, st)) != cudaSuccess)
             return cuda_status(e);
         if ((s = solver_adjoint(S, S->delta, S->gx, ev ? ev + 3 : nullptr, st)) != GPAIR_OK) return s;
-        if (S->vcrF &&   // grad_x += lambda grad R_VCR(x); R_VCR(x) into res[4]
-            (e = launch_vcr(S->x, S->g.nx, S->g.ny, S->g.nz, S->p.vcr_beta, S->p.vcr_eps, S->p.vcr_lambda, S->vcrF,
-                            partial, res + 4, S->gx, st)) != cudaSuccess)
+        if (S->vcr &&    // grad_x += lambda grad R_VCR(x); R_VCR(x) into res[4]
+            (e = launch_vcr(S->x, S->g.nx, S->g.ny, S->g.nz, S->p.vcr_beta, S->p.vcr_eps, S->p.vcr_lambda, partial,
+                            res + 4, S->gx, st)) != cudaSuccess)
             return cuda_status(e);
         const int tt = S->t + 1;
         const double c1 = 1.0 - std::pow((double)S->p.beta1, tt), c2 = 1.0 - std::pow((double)S->p.beta2, tt);
@@ -928,7 +925,7 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
         double h[5] = {0, 0, 0, 0, 0};
         if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
-        const double reg = S->vcrF ? (double)S->p.vcr_lambda * h[4] : 0.0;
+        const double reg = S->vcr ? (double)S->p.vcr_lambda * h[4] : 0.0;
         if (loss_out) *loss_out = h[0] / (double)N + reg;
         if (resid_out) *resid_out = std::sqrt(h[0]);
     }

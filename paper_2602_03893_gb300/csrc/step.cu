@@ -173,52 +173,24 @@ __device__ __forceinline__ int64_t vox(int ix, int iy, int iz, int nx, int ny) {
     return ((int64_t)iz * ny + iy) * nx + ix;
 }
 
-// Pass 1: per voxel the derivative terms and the weighted fields
+// One fused pass per tile of VT_X x VT_Y x VT_Z voxels.  The CTA stages x on the tile plus two
+// voxels per side (neighbour indices clamped per axis), forms the weighted fields
 //   F_k = m_k (D_k x) / sqrt(sH + eps)  (k = xx, yy, zz, xy, xz, yz; m = 1, 1, 1, 2, 2, 2),
 //   F_{6+d} = beta (D_d x) / sqrt(sT + eps),
-// sH = sum_{p,q} (D_pq x)^2, sT = sum_d (D_d x)^2; partial[blk] = sum sqrt(sH + eps) + beta sqrt(sT + eps).
-__global__ void __launch_bounds__(RED_THREADS)
-vcr_fields_kernel(const float* __restrict__ x, int nx, int ny, int nz, float beta, float eps, float* __restrict__ F,
-                  double* __restrict__ partial) {
-    __shared__ double red[RED_THREADS / 32];
-    const int64_t M = (int64_t)nx * ny * nz;
-    double acc = 0.0;
-    // blocks stride over (y, z) rows, threads over x: no per-voxel index division
-    for (int row = blockIdx.x; row < ny * nz; row += gridDim.x)
-    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
-        const int iy = row % ny, iz = row / ny;
-        const int64_t i = (int64_t)row * nx + ix;
-        const int xm = max(ix - 1, 0), xp = min(ix + 1, nx - 1);
-        const int ym = max(iy - 1, 0), yp = min(iy + 1, ny - 1);
-        const int zm = max(iz - 1, 0), zp = min(iz + 1, nz - 1);
-        auto at = [&](int a, int b, int c) { return __ldg(x + vox(a, b, c, nx, ny)); };
-        const float c0 = x[i];
-        const float vxp = at(xp, iy, iz), vxm = at(xm, iy, iz);
-        const float vyp = at(ix, yp, iz), vym = at(ix, ym, iz);
-        const float vzp = at(ix, iy, zp), vzm = at(ix, iy, zm);
-        const float d1x = 0.5f * (vxp - vxm), d1y = 0.5f * (vyp - vym), d1z = 0.5f * (vzp - vzm);
-        const float hxx = (vxp - c0) + (vxm - c0), hyy = (vyp - c0) + (vym - c0), hzz = (vzp - c0) + (vzm - c0);
-        const float hxy = 0.25f * ((at(xp, yp, iz) - at(xp, ym, iz)) - (at(xm, yp, iz) - at(xm, ym, iz)));
-        const float hxz = 0.25f * ((at(xp, iy, zp) - at(xp, iy, zm)) - (at(xm, iy, zp) - at(xm, iy, zm)));
-        const float hyz = 0.25f * ((at(ix, yp, zp) - at(ix, yp, zm)) - (at(ix, ym, zp) - at(ix, ym, zm)));
-        const float sH = hxx * hxx + hyy * hyy + hzz * hzz + 2.f * (hxy * hxy + hxz * hxz + hyz * hyz);
-        const float sT = d1x * d1x + d1y * d1y + d1z * d1z;
-        const float rH = sqrtf(sH + eps), rT = sqrtf(sT + eps);
-        const float wH = 1.f / rH, wT = beta / rT;
-        F[i] = wH * hxx;
-        F[M + i] = wH * hyy;
-        F[2 * M + i] = wH * hzz;
-        F[3 * M + i] = 2.f * wH * hxy;
-        F[4 * M + i] = 2.f * wH * hxz;
-        F[5 * M + i] = 2.f * wH * hyz;
-        F[6 * M + i] = wT * d1x;
-        F[7 * M + i] = wT * d1y;
-        F[8 * M + i] = wT * d1z;
-        acc += (double)rH + (double)beta * (double)rT;
-    }
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
+// sH = sum_{p,q} (D_pq x)^2, sT = sum_d (D_d x)^2, on the tile plus one voxel per side, and adds
+// lam (sum_k D_k^T F_k) to g on the tile.  (D^T F)[j] sums c F[i] over the stencil entries (o, c)
+// and every i whose clamped neighbour i + o is j; inside the volume that is i = j - o, and on a
+// face the clamp adds i = j.  Only x and g cross HBM; the fields stay in shared memory.  The
+// value sum sqrt(sH + eps) + beta sqrt(sT + eps) of the tile's own voxels goes into the CTA's FP64
+// partial.
+constexpr int VT_X = 32, VT_Y = 4, VT_Z = 4;
+constexpr int VX_X = VT_X + 4, VX_Y = VT_Y + 4, VX_Z = VT_Z + 4;    // staged x
+constexpr int VF_X = VT_X + 2, VF_Y = VT_Y + 2, VF_Z = VT_Z + 2;    // staged fields
+constexpr int VF_N = VF_X * VF_Y * VF_Z;
+struct VcrSmem {
+    float xs[VX_Z][VX_Y][VX_X];
+    float F[9][VF_N];
+};
 
 // Stencil entries of the nine operators: field k, neighbour offset, coefficient.
 struct VcrEntry {
@@ -237,60 +209,189 @@ __constant__ VcrEntry c_vcr[27] = {
     {8, 0, 0, 1, .5f}, {8, 0, 0, -1, -.5f},
 };
 
-// Coordinates i in [0, n) with clamp(i + o) == j (o in {-1, 0, 1}): at most two.
-__device__ __forceinline__ int vcr_preimage(int j, int o, int n, int* out) {
-    int c = 0;
-    for (int i = j - o - 1; i <= j - o + 1; ++i)
-        if (i >= 0 && i < n && min(max(i + o, 0), n - 1) == j) out[c++] = i;
-    return c;
+// Extra terms of (sum_k D_k^T F_k)[j] for a voxel on a face of the volume.  Along one axis the
+// preimages of j under the clamped offset o are j - o (when inside) and j itself when j + o falls
+// outside; the gather over j - o with zero fields outside the volume already holds the products
+// of the first kind, so this adds every product that takes j itself along at least one axis.
+__device__ __noinline__ float vcr_fold_terms(const float* F, int jx, int jy, int jz, int nx, int ny, int nz, int X0,
+                                             int Y0, int Z0) {
+    float s = 0.f;
+    for (int e = 0; e < 27; ++e) {
+        const VcrEntry E = c_vcr[e];
+        const bool fx = jx + E.ox < 0 || jx + E.ox >= nx, fy = jy + E.oy < 0 || jy + E.oy >= ny,
+                   fz = jz + E.oz < 0 || jz + E.oz >= nz;
+        if (!(fx || fy || fz)) continue;
+        float sum = 0.f;
+        for (int m = 1; m < 8; ++m) {          // bit set: that axis takes j itself
+            if (((m & 1) && !fx) || ((m & 2) && !fy) || ((m & 4) && !fz)) continue;
+            const int px = (m & 1) ? jx : jx - E.ox, py = (m & 2) ? jy : jy - E.oy, pz = (m & 4) ? jz : jz - E.oz;
+            // an axis that shifts outside the volume reads a zero field: skip it
+            if (px < 0 || px >= nx || py < 0 || py >= ny || pz < 0 || pz >= nz) continue;
+            sum += F[E.k * VF_N + ((pz - Z0 + 1) * VF_Y + (py - Y0 + 1)) * VF_X + (px - X0 + 1)];
+        }
+        s = fmaf(E.c, sum, s);
+    }
+    return s;
 }
 
-// Pass 2: g[j] += lam (sum_k D_k^T F_k)[j].  (D^T F)[j] = sum over the stencil entries (o, c) of
-// c F[i] over every i whose clamped neighbour i + o is j; inside the volume that is i = j - o.
+template <bool GRAD>
 __global__ void __launch_bounds__(RED_THREADS, 4)
-vcr_grad_kernel(const float* __restrict__ F, int nx, int ny, int nz, float lam, float* __restrict__ g) {
-    const int64_t M = (int64_t)nx * ny * nz;
-    for (int row = blockIdx.x; row < ny * nz; row += gridDim.x)
-    for (int jx = threadIdx.x; jx < nx; jx += blockDim.x) {
-        const int jy = row % ny, jz = row / ny;
-        const int64_t j = (int64_t)row * nx + jx;
-        float acc = 0.f;
-        if (jx > 0 && jx < nx - 1 && jy > 0 && jy < ny - 1 && jz > 0 && jz < nz - 1) {
-#pragma unroll
-            for (int e = 0; e < 27; ++e) {
-                const VcrEntry E = c_vcr[e];
-                acc = fmaf(E.c, __ldg(F + E.k * M + (j - (E.ox + (int64_t)E.oy * nx + (int64_t)E.oz * nx * ny))), acc);
-            }
-        } else {
-            for (int e = 0; e < 27; ++e) {
-                const VcrEntry E = c_vcr[e];
-                int px[2], py[2], pz[2];
-                const int cx = vcr_preimage(jx, E.ox, nx, px), cy = vcr_preimage(jy, E.oy, ny, py),
-                          cz = vcr_preimage(jz, E.oz, nz, pz);
-                float s = 0.f;
-                for (int a = 0; a < cx; ++a)
-                    for (int b = 0; b < cy; ++b)
-                        for (int c = 0; c < cz; ++c) s += __ldg(F + E.k * M + vox(px[a], py[b], pz[c], nx, ny));
-                acc = fmaf(E.c, s, acc);
-            }
+vcr_fused_kernel(const float* __restrict__ x, int nx, int ny, int nz, float beta, float eps, float lam,
+                 float* __restrict__ g, double* __restrict__ partial, unsigned tile_mul) {
+    extern __shared__ __align__(16) unsigned char vcr_smem[];
+    VcrSmem& S = *reinterpret_cast<VcrSmem*>(vcr_smem);
+    __shared__ double red[RED_THREADS / 32];
+    __shared__ int tile_org[3];
+    const unsigned ntx = (nx + VT_X - 1) / VT_X, nty = (ny + VT_Y - 1) / VT_Y, ntz = (nz + VT_Z - 1) / VT_Z;
+    const unsigned ntiles = ntx * nty * ntz;                  // < 2^31 (checked on the host)
+    // Tile k of this CTA is t = (blockIdx.x + k gridDim.x) tile_mul mod ntiles, stepped by one add:
+    // tile_mul is coprime to ntiles, so every tile is visited once, and the face tiles, which carry
+    // extra terms, spread over the CTAs instead of one x column staying with a CTA for good.
+    const unsigned step = (unsigned)(((unsigned long long)gridDim.x * tile_mul) % ntiles);
+    unsigned t = (unsigned)(((unsigned long long)blockIdx.x * tile_mul) % ntiles);
+    KahanF acc;    // this thread's own voxels; FP64 from the CTA sum on
+    for (unsigned tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const unsigned tx = t % ntx, rest = t / ntx;
+            tile_org[0] = (int)tx * VT_X;
+            tile_org[1] = (int)(rest % nty) * VT_Y;
+            tile_org[2] = (int)(rest / nty) * VT_Z;
         }
-        g[j] = fmaf(lam, acc, g[j]);
+        t += step;
+        if (t >= ntiles) t -= ntiles;
+        __syncthreads();   // the previous tile's readers are done with S; tile_org is published
+        const int X0 = tile_org[0], Y0 = tile_org[1], Z0 = tile_org[2];
+        for (int q = threadIdx.x; q < VX_X * VX_Y * VX_Z; q += RED_THREADS) {
+            const int a = q % VX_X, b = (q / VX_X) % VX_Y, c = q / (VX_X * VX_Y);
+            const int ix = min(max(X0 - 2 + a, 0), nx - 1), iy = min(max(Y0 - 2 + b, 0), ny - 1),
+                      iz = min(max(Z0 - 2 + c, 0), nz - 1);
+            S.xs[c][b][a] = __ldg(x + vox(ix, iy, iz, nx, ny));
+        }
+        __syncthreads();
+        // fields at the positions of the tile +- 1 that lie in the volume; the staged x entry of a
+        // position (a, b, c) of the field grid is (a + 1, b + 1, c + 1)
+        for (int q = threadIdx.x; q < VF_N; q += RED_THREADS) {
+            const int a = q % VF_X, b = (q / VF_X) % VF_Y, c = q / (VF_X * VF_Y);
+            const int px = X0 - 1 + a, py = Y0 - 1 + b, pz = Z0 - 1 + c;
+            const bool inside = px >= 0 && px < nx && py >= 0 && py < ny && pz >= 0 && pz < nz;
+            const bool own = inside && a >= 1 && a <= VT_X && b >= 1 && b <= VT_Y && c >= 1 && c <= VT_Z;
+            if (!inside) {      // zero fields outside the volume: the interior gather then needs no masks
+                if (GRAD)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) S.F[k][q] = 0.f;
+                continue;
+            }
+            if (!GRAD && !own) continue;
+            auto at = [&](int dx, int dy, int dz) { return S.xs[c + 1 + dz][b + 1 + dy][a + 1 + dx]; };
+            const float c0 = at(0, 0, 0);
+            const float vxp = at(1, 0, 0), vxm = at(-1, 0, 0);
+            const float vyp = at(0, 1, 0), vym = at(0, -1, 0);
+            const float vzp = at(0, 0, 1), vzm = at(0, 0, -1);
+            const float d1x = 0.5f * (vxp - vxm), d1y = 0.5f * (vyp - vym), d1z = 0.5f * (vzp - vzm);
+            const float hxx = (vxp - c0) + (vxm - c0), hyy = (vyp - c0) + (vym - c0), hzz = (vzp - c0) + (vzm - c0);
+            const float hxy = 0.25f * ((at(1, 1, 0) - at(1, -1, 0)) - (at(-1, 1, 0) - at(-1, -1, 0)));
+            const float hxz = 0.25f * ((at(1, 0, 1) - at(1, 0, -1)) - (at(-1, 0, 1) - at(-1, 0, -1)));
+            const float hyz = 0.25f * ((at(0, 1, 1) - at(0, 1, -1)) - (at(0, -1, 1) - at(0, -1, -1)));
+            const float sH = hxx * hxx + hyy * hyy + hzz * hzz + 2.f * (hxy * hxy + hxz * hxz + hyz * hyz);
+            const float sT = d1x * d1x + d1y * d1y + d1z * d1z;
+            if (GRAD) {
+                const float wH = rsqrtf(sH + eps), wT = beta * rsqrtf(sT + eps);
+                S.F[0][q] = wH * hxx;
+                S.F[1][q] = wH * hyy;
+                S.F[2][q] = wH * hzz;
+                S.F[3][q] = 2.f * wH * hxy;
+                S.F[4][q] = 2.f * wH * hxz;
+                S.F[5][q] = 2.f * wH * hyz;
+                S.F[6][q] = wT * d1x;
+                S.F[7][q] = wT * d1y;
+                S.F[8][q] = wT * d1z;
+            }
+            if (own) acc.add(sqrtf(sH + eps) + beta * sqrtf(sT + eps));
+        }
+        if (!GRAD) continue;
+        __syncthreads();
+        for (int q = threadIdx.x; q < VT_X * VT_Y * VT_Z; q += RED_THREADS) {
+            const int a = q % VT_X, b = (q / VT_X) % VT_Y, c = q / (VT_X * VT_Y);
+            const int jx = X0 + a, jy = Y0 + b, jz = Z0 + c;
+            if (jx >= nx || jy >= ny || jz >= nz) continue;
+            const int f0 = ((c + 1) * VF_Y + (b + 1)) * VF_X + (a + 1);
+            // the entries of c_vcr with i = j - o, written out (zero fields outside the volume)
+            constexpr int SY = VF_X, SZ = VF_X * VF_Y;
+            const float* F0 = S.F[0] + f0;
+            const float* F1 = S.F[1] + f0;
+            const float* F2 = S.F[2] + f0;
+            const float* F3 = S.F[3] + f0;
+            const float* F4 = S.F[4] + f0;
+            const float* F5 = S.F[5] + f0;
+            const float* F6 = S.F[6] + f0;
+            const float* F7 = S.F[7] + f0;
+            const float* F8 = S.F[8] + f0;
+            float s = (F0[-1] + F0[1]) - 2.f * F0[0];
+            s += (F1[-SY] + F1[SY]) - 2.f * F1[0];
+            s += (F2[-SZ] + F2[SZ]) - 2.f * F2[0];
+            s += 0.25f * ((F3[-1 - SY] - F3[-1 + SY]) - (F3[1 - SY] - F3[1 + SY]));
+            s += 0.25f * ((F4[-1 - SZ] - F4[-1 + SZ]) - (F4[1 - SZ] - F4[1 + SZ]));
+            s += 0.25f * ((F5[-SY - SZ] - F5[-SY + SZ]) - (F5[SY - SZ] - F5[SY + SZ]));
+            s += 0.5f * (F6[-1] - F6[1]);
+            s += 0.5f * (F7[-SY] - F7[SY]);
+            s += 0.5f * (F8[-SZ] - F8[SZ]);
+            const int fxs = jx == 0 ? -1 : (jx == nx - 1 ? 1 : 0);   // outward offset on a face, else 0
+            const int fys = jy == 0 ? -1 : (jy == ny - 1 ? 1 : 0);
+            const int fzs = jz == 0 ? -1 : (jz == nz - 1 ? 1 : 0);
+            const int nf = (fxs != 0) + (fys != 0) + (fzs != 0);
+            if (nf == 1 && (fxs ? nx : fys ? ny : nz) > 1) {
+                // one face, axis a with outward offset sg: the entries whose offset along a is sg also
+                // take j itself along a (the other axes shift as inside, zero fields outside)
+                const float sg = 0.25f * (float)(fxs + fys + fzs);
+                if (fxs) s += F0[0] + sg * ((F3[-SY] - F3[SY]) + (F4[-SZ] - F4[SZ]) + 2.f * F6[0]);
+                else if (fys) s += F1[0] + sg * ((F3[-1] - F3[1]) + (F5[-SZ] - F5[SZ]) + 2.f * F7[0]);
+                else s += F2[0] + sg * ((F4[-1] - F4[1]) + (F5[-SY] - F5[SY]) + 2.f * F8[0]);
+            } else if (nf != 0) {
+                s += vcr_fold_terms(S.F[0], jx, jy, jz, nx, ny, nz, X0, Y0, Z0);
+            }
+            const int64_t j = vox(jx, jy, jz, nx, ny);
+            g[j] = fmaf(lam, s, g[j]);
+        }
     }
+    const double tot = block_sum((double)acc.s - (double)acc.c, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
+
+int64_t vcr_tiles(int nx, int ny, int nz) {
+    return (int64_t)((nx + VT_X - 1) / VT_X) * ((ny + VT_Y - 1) / VT_Y) * ((nz + VT_Z - 1) / VT_Z);
+}
+
+// Multiplier of the tile permutation: an odd prime that does not divide the tile count.
+unsigned vcr_tile_mul(int nx, int ny, int nz) {
+    const int64_t n = vcr_tiles(nx, ny, nz);
+    const int64_t primes[] = {7919, 7927, 7933, 7937, 7949};
+    for (int64_t p : primes)
+        if (n % p != 0) return p % n == 0 ? 1u : (unsigned)p;
+    return 1u;
+}
+
+size_t vcr_smem_bytes(bool grad) { return grad ? sizeof(VcrSmem) : sizeof(float) * VX_X * VX_Y * VX_Z; }
 
 // value_out (device, may be NULL): R_VCR(x) in FP64.  g (may be NULL): g += lam grad R_VCR(x).
-// F: 9 M floats of scratch; partial: RED_BLOCKS doubles.
-cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, float* F,
-                       double* partial, double* value_out, float* g, cudaStream_t st) {
-    vcr_fields_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, nx, ny, nz, beta, eps, F, partial);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+// partial: RED_BLOCKS doubles.
+cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, double* partial,
+                       double* value_out, float* g, cudaStream_t st) {
+    if (vcr_tiles(nx, ny, nz) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (g) {
+        const size_t sm = vcr_smem_bytes(true);
+        if ((e = cudaFuncSetAttribute(vcr_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        vcr_fused_kernel<true><<<RED_BLOCKS, RED_THREADS, sm, st>>>(x, nx, ny, nz, beta, eps, lam, g, partial,
+                                                                    vcr_tile_mul(nx, ny, nz));
+    } else {
+        vcr_fused_kernel<false><<<RED_BLOCKS, RED_THREADS, vcr_smem_bytes(false), st>>>(
+            x, nx, ny, nz, beta, eps, lam, nullptr, partial, vcr_tile_mul(nx, ny, nz));
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (value_out) {
         finish_kernel<<<1, RED_THREADS, 0, st>>>(partial, RED_BLOCKS, 1, 1, value_out);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (g) {
-        vcr_grad_kernel<<<RED_BLOCKS * 8, RED_THREADS, 0, st>>>(F, nx, ny, nz, lam, g);
         e = cudaGetLastError();
     }
     return e;
