@@ -9,6 +9,13 @@
 // keeps its sensor's impulse line over the slab's band on the fine grid in shared memory and
 // adds every pair's mass there with a shared-memory atomic; after the slab it convolves and
 // decimates the band into the slab's partial row (summed over slabs by slab_reduce_kernel).
+// The adds are 32-bit integer adds of the mass in fixed point, which the shared-memory units
+// execute at about twice the rate of float adds.  A warp scales its masses by
+// q = ASSA_QMAX d_min / max|A|, d_min the sensor's distance to the slab's box, so that each
+// scaled mass is below ASSA_QMAX = 2^19 in magnitude, and every ASSA_FLUSH bricks (at most
+// 2^12 pairs) it converts the integer band into a float band and clears it: no band value can
+// leave the int32 range, and each mass is rounded to 2^-19 of the largest.  A warp whose sensor
+// touches the slab's box, or a non-finite max|A|, keeps float adds.
 // Adjoint: the correlated residual dconv_j[k] = sum_n h[alpha n - k] delta_j[n] is formed once
 // per sensor (assa_dconv_kernel); then one thread per Gaussian gathers dconv at its snapped
 // samples over all sensors, Kahan-compensated, and writes its gradient once.
@@ -25,6 +32,8 @@ constexpr int ASSA_SPC = 8;
 constexpr int ASSA_THREADS = 32 * ASSA_SPC;
 constexpr int ASSA_RING = 4;
 constexpr int ASSA_ADJ_SC = 32;
+constexpr float ASSA_QMAX = 0.99f * 524288.f;      // 0.99 * 2^19: bound of a scaled mass
+constexpr int ASSA_FLUSH = 16;                     // bricks per integer band (16 * 256 = 2^12 pairs)
 
 struct AssaSmem {
     float tileA[ASSA_RING][TILE];
@@ -56,10 +65,20 @@ __device__ __forceinline__ int assa_an0(int alpha, int n0) {
     return (int)max(min(an, (long long)(1 << 30)), -(long long)(1 << 30));
 }
 
+// max |A| over the amplitudes, as the bits of a non-negative float (ordered like the floats;
+// a NaN amplitude gives a NaN).  *out must be zero before the launch.
+__global__ void assa_amax_kernel(const float* __restrict__ A, int64_t M, unsigned* __restrict__ out) {
+    unsigned m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned)__float_as_int(fabsf(A[i])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 __global__ void __launch_bounds__(ASSA_THREADS)
 assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
                 int2* __restrict__ rows, int LB, int* status, int use_tma, const __grid_constant__ CUtensorMap tmap,
-                const __grid_constant__ AssaTable T) {
+                const __grid_constant__ AssaTable T, const unsigned* __restrict__ amax_bits) {
     static_assert(BX == 8 && BY == 8 && BZ == 4 && TILE == 256,
                   "lane offsets below assume lane + 32 q -> (lane & 7, (lane >> 3) + 4 (q & 1), q >> 1)");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -67,7 +86,8 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int alpha = T.alpha, K = T.K;
     const int ZB = assa_zb(LB, alpha, K);
-    float* zb = reinterpret_cast<float*>(smem_raw + ASSA_HDR) + (size_t)warp * ZB;
+    float* zb = reinterpret_cast<float*>(smem_raw + ASSA_HDR) + (size_t)warp * 2 * ZB;   // float band
+    int* zi = reinterpret_cast<int*>(zb + ZB);                                          // fixed-point band
 
     const int slab = blockIdx.y;
     const int j = blockIdx.x * ASSA_SPC + warp;
@@ -82,11 +102,14 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
     // a fine step of snapping
     float sx = 0.f, sy = 0.f, sz = 0.f;
     int n_lo = 0, n_hi = -1;
+    float qscale = 0.f;                    // 0: float adds
     if (has_sensor) {
         sx = a.xyz[3 * j]; sy = a.xyz[3 * j + 1]; sz = a.xyz[3 * j + 2];
         if (nTiles > 0) {
             double dmin, dmax;
             box_distance(sl, sx, sy, sz, dmin, dmax);
+            const float amax = __int_as_float((int)*amax_bits);
+            if (amax > 0.f && amax <= 3.0e38f && dmin > 0.0) qscale = (float)((double)ASSA_QMAX * dmin / (double)amax);
             double ks = (double)a.k * sl.smax;
             double lo = floor(((dmin - ks) / a.v - a.t0) * a.fs) - 2.0;
             double hi = ceil(((dmax + ks) / a.v - a.t0) * a.fs) + 2.0;
@@ -111,7 +134,24 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
         }
         fence_mbar_init();
     }
-    for (int q = lane; q < ZB; q += 32) zb[q] = 0.f;
+    for (int q = lane; q < ZB; q += 32) {
+        zb[q] = 0.f;
+        zi[q] = 0;
+    }
+    const bool fixedp = qscale > 0.f;     // warp-uniform
+    const float inv_q = fixedp ? 1.f / qscale : 0.f;
+    // integer band -> float band, cleared for the next bricks
+    auto flush = [&]() {
+        __syncwarp();
+        for (int q = lane; q < ZB; q += 32) {
+            const int v = zi[q];
+            if (v != 0) {
+                zb[q] = fmaf((float)v, inv_q, zb[q]);
+                zi[q] = 0;
+            }
+        }
+        __syncwarp();
+    };
     __syncthreads();
 
     const bool tma = use_tma != 0;
@@ -183,8 +223,14 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
                 // snapped fine sample: floor((R / v - t0) alpha fs + 1/2) = alpha n0 + floor(phi alpha / Delta + 1/2)
                 const int k = assa_snap(phi, aInvD, base);
                 const int kb = k - kb0;
-                if (Ai != 0.f && k >= 0 && k < Nup && kb >= 0 && kb < ZB) atomicAdd(&zb[kb], Ai * invR);
+                if (Ai != 0.f && k >= 0 && k < Nup && kb >= 0 && kb < ZB) {
+                    if (fixedp)   // round(A / r q): |.| < 2^19, so the float representation gives it
+                        atomicAdd(&zi[kb], __float_as_int(fmaf(Ai * invR, qscale, SNAP_MAGIC)) - (int)SNAP_BITS);
+                    else
+                        atomicAdd(&zb[kb], Ai * invR);
+                }
             }
+            if (fixedp && (t + 1) % ASSA_FLUSH == 0) flush();
         }
         // release the slot; the warp that releases it last refills it with tile t + ASSA_RING
         __syncwarp();
@@ -209,6 +255,7 @@ assa_fwd_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float*
         return;
     }
     if (active) {
+        if (fixedp) flush();
         // y[n] = sum_m z[m] h[alpha n - m]; sample n = w + q needs zb[alpha q .. alpha q + 2K]
         const int wend = min(a.Nt, w + LB);
         for (int q = lane; q < wend - w; q += 32) {
@@ -303,21 +350,25 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
 // ---- host side -----------------------------------------------------------------------------
 
 size_t assa_fwd_smem(int LB, const AssaTable& T) {
-    return ASSA_HDR + (size_t)ASSA_SPC * assa_zb(LB, T.alpha, T.K) * sizeof(float);
+    return ASSA_HDR + (size_t)ASSA_SPC * 2 * assa_zb(LB, T.alpha, T.K) * sizeof(float);
 }
 
-// ev (optional): two events recorded immediately before and after the main kernel.
+// ev (optional): two events recorded immediately before and after the main kernel.  amax: 4 bytes
+// of device scratch for max |A|.
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
-                                const cudaEvent_t* ev, cudaStream_t st) {
+                                unsigned* amax, const cudaEvent_t* ev, cudaStream_t st) {
     static const CUtensorMap zero_map = [] { CUtensorMap z; memset(&z, 0, sizeof(z)); return z; }();
     const size_t smem = assa_fwd_smem(LB, T);
     cudaError_t e = cudaFuncSetAttribute(assa_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+    assa_amax_kernel<<<4 * 152, 256, 0, st>>>(g.A, g.M, amax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 grid((a.Nd + ASSA_SPC - 1) / ASSA_SPC, S);
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     assa_fwd_kernel<<<grid, ASSA_THREADS, smem, st>>>(g, a, si, partial, rows, LB, status, tmap != nullptr,
-                                                      tmap ? *tmap : zero_map, T);
+                                                      tmap ? *tmap : zero_map, T, amax);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     return e;

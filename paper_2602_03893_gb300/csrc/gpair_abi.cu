@@ -38,7 +38,7 @@ cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float
                        double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
                                 int2* rows, int LB, int* status, const CUtensorMap* tmap, const AssaTable& T,
-                                const cudaEvent_t* ev, cudaStream_t st);
+                                unsigned* amax, const cudaEvent_t* ev, cudaStream_t st);
 size_t assa_dconv_bytes(const ArrDev& a, const AssaTable& T);
 cudaError_t launch_assa_adjoint(const GaussDev& g, const ArrDev& a, const float* delta, float* gA, const AssaTable& T,
                                 float* dconv, const cudaEvent_t* ev, cudaStream_t st);
@@ -584,7 +584,10 @@ ArrDev assa_band_array(const GaussDev& g, const ArrDev& a, const AssaTable& T) {
     return aa;
 }
 
-// ASSA forward into y with scratch of p.bytes (p = plan_forward(g, assa_band_array(...))).
+// Scratch of the ASSA forward beyond the plan: max |A| for the fixed-point bands.
+constexpr size_t ASSA_EXTRA_BYTES = 256;
+
+// ASSA forward into y with scratch of p.bytes + ASSA_EXTRA_BYTES (p = plan_forward(g, assa_band_array(...))).
 gpair_status run_assa_forward(const GaussDev& g, const ArrDev& aa, const AssaTable& T, const FwdPlan& p, float* y,
                               void* scratch, int* status, const cudaEvent_t* ev, cudaStream_t st) {
     char* base = static_cast<char*>(scratch);
@@ -596,7 +599,8 @@ gpair_status run_assa_forward(const GaussDev& g, const ArrDev& aa, const AssaTab
     const bool tma = make_tmap(g, &map);
     cudaError_t e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
     if (e == cudaSuccess)
-        e = launch_assa_forward(g, aa, si, p.S, part, rows, p.LB, status, tma ? &map : nullptr, T, ev, st);
+        e = launch_assa_forward(g, aa, si, p.S, part, rows, p.LB, status, tma ? &map : nullptr, T,
+                                reinterpret_cast<unsigned*>(base + p.bytes), ev, st);
     if (e == cudaSuccess) e = launch_slab_reduce(g, aa, part, rows, p.S, p.PL, y, st);
     return cuda_status(e);
 }
@@ -613,7 +617,7 @@ gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai
     FwdPlan p = plan_forward(g, aa);
     void* scratch = nullptr;
     int* status = nullptr;
-    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    if ((s = get_scratch(st, p.bytes + ASSA_EXTRA_BYTES, &scratch, &status)) != GPAIR_OK) return s;
     return run_assa_forward(g, aa, T, p, y, scratch, status, nullptr, st);
 }
 
@@ -814,7 +818,7 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               cudaMalloc(&S->delta, N * 4) == cudaSuccess &&
               (prm->rule != GPAIR_RULE_GD_LINESEARCH || cudaMalloc(&S->Fg, N * 4) == cudaSuccess) &&
               cudaMalloc(&S->red, sizeof(double) * (2 * red_blocks() + 8)) == cudaSuccess &&
-              cudaMalloc(&S->fwd_scratch, S->plan.bytes) == cudaSuccess &&
+              cudaMalloc(&S->fwd_scratch, S->plan.bytes + (assa ? ASSA_EXTRA_BYTES : 0)) == cudaSuccess &&
               (qbytes == 0 || cudaMalloc(&S->qbuf, qbytes) == cudaSuccess) &&
               (!assa || cudaMalloc(&S->dconv, assa_dconv_bytes(a, S->T)) == cudaSuccess) &&
               cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;

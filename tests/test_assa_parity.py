@@ -128,3 +128,16 @@ def test_free_gaussians_are_rejected():
                        free=synth.free_gaussians(g, 3, A=np.ones(g.M)))
     with pytest.raises(_lib.GpairError):
         gpu_assa_forward(w)
+
+
+def test_sensor_inside_a_slab_box_and_wide_amplitude_range():
+    """The band adds are 32-bit fixed point scaled per (slab, sensor) by the sensor's distance to
+    the slab's box; a sensor inside the box keeps float adds.  Amplitudes spanning six decades
+    check that rounding to 2^-19 of the largest scaled mass stays within the tolerance."""
+    g = synth.centred_grid(16, 12, 8, 0.1e-3)
+    rng = np.random.default_rng(12)
+    A = (10.0 ** rng.uniform(-6.0, 0.0, g.M)).astype(np.float32)
+    sens = synth.cap_sensors(12, 8e-3, 150.0)
+    inside = np.array([[0.23e-3, -0.17e-3, 0.11e-3]], dtype=np.float32)     # within the grid's box
+    w = synth.Workload("inside", g, np.concatenate([sens, inside]), 512, A=A)
+    _check_forward(w, A=A)
