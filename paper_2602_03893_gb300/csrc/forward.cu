@@ -997,6 +997,56 @@ __global__ void slab_reduce_kernel(const float* __restrict__ partial, const int2
     }
 }
 
+// Banded rows with the sensor's row descriptors staged in shared memory (S of them): a block
+// covers 256 samples of one sensor, leaves at once when no band reaches them, and skips the
+// slabs whose band misses them without touching their rows.  Each sample sums its slabs in
+// slab order, as slab_reduce_kernel does.
+constexpr int SLAB_RED_THREADS = 256;
+constexpr int SLAB_RED_MAX_S = 6144;        // 48 KB of row descriptors
+__global__ void __launch_bounds__(SLAB_RED_THREADS)
+slab_reduce_banded_kernel(const float* __restrict__ partial, const int2* __restrict__ rows, int S, int Nd, int Nt,
+                          int PL, float* __restrict__ y) {
+    extern __shared__ int2 srow[];
+    __shared__ int ext[2];
+    const int j = blockIdx.y;
+    const int n0 = blockIdx.x * SLAB_RED_THREADS;
+    if (threadIdx.x == 0) {
+        ext[0] = INT_MAX;
+        ext[1] = INT_MIN;
+    }
+    __syncthreads();
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int q = threadIdx.x; q < S; q += SLAB_RED_THREADS) {
+        const int2 ri = rows[(size_t)q * Nd + j];
+        srow[q] = ri;
+        if (ri.y > 0) {
+            lo = min(lo, ri.x);
+            hi = max(hi, ri.x + ri.y);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ext[0], lo);
+        atomicMax(&ext[1], hi);
+    }
+    __syncthreads();
+    const int n = n0 + (int)threadIdx.x;
+    float acc = 0.f;
+    if (ext[0] < n0 + SLAB_RED_THREADS && ext[1] > n0) {
+        const int nend = n0 + SLAB_RED_THREADS;
+        for (int q = 0; q < S; ++q) {
+            const int2 ri = srow[q];
+            if (ri.x >= nend || ri.x + ri.y <= n0) continue;     // the same for the whole block
+            const unsigned d = (unsigned)(n - ri.x);
+            if (d < (unsigned)ri.y) acc += partial[((size_t)q * Nd + j) * PL + d];
+        }
+    }
+    if (n < Nt) y[(size_t)j * Nt + n] = acc;
+}
+
 // ------------------------------------------------------------------------------------------
 // Host side.
 
@@ -1086,7 +1136,11 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st) {
     dim3 rgrid((a.Nt + 255) / 256, a.Nd);
-    slab_reduce_kernel<<<rgrid, 256, 0, st>>>(partial, rows, S, a.Nd, a.Nt, PL, g.grid ? 1 : 0, y);
+    if (g.grid && S <= SLAB_RED_MAX_S)
+        slab_reduce_banded_kernel<<<rgrid, SLAB_RED_THREADS, (size_t)S * sizeof(int2), st>>>(partial, rows, S, a.Nd,
+                                                                                             a.Nt, PL, y);
+    else
+        slab_reduce_kernel<<<rgrid, 256, 0, st>>>(partial, rows, S, a.Nd, a.Nt, PL, g.grid ? 1 : 0, y);
     return cudaGetLastError();
 }
 
