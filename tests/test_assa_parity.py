@@ -141,3 +141,19 @@ def test_sensor_inside_a_slab_box_and_wide_amplitude_range():
     inside = np.array([[0.23e-3, -0.17e-3, 0.11e-3]], dtype=np.float32)     # within the grid's box
     w = synth.Workload("inside", g, np.concatenate([sens, inside]), 512, A=A)
     _check_forward(w, A=A)
+
+
+def test_paper_scale_adjoint_sampled_gaussians():
+    """The benchmark's launch (8.4 M Gaussians x 1024 sensors, alpha = 2); the oracle recomputes
+    2000 sampled Gaussians' gradients over all sensors (each entry is independent)."""
+    w = synth.paper_scale(3)
+    rng = np.random.default_rng(13)
+    delta = rng.normal(size=(w.Nd, w.Nt)).astype(np.float32)
+    idx = np.sort(rng.choice(w.M, 2000, replace=False))
+    g = gpu_assa_adjoint(w, delta)
+    assert np.all(np.isfinite(g))
+    G = oracle_gaussians(w)
+    Gs = oracle.Gaussians(G.c[idx], G.sigma[idx], G.A[idx])
+    g_ora, amb = oracle.assa_adjoint(Gs, G.sigma[0], w.sensors, w.v, w.fs, w.t0, w.Nt, delta, tau=TAU_SNAP,
+                                     want_amb=True)
+    assert np.linalg.norm(g[idx] - g_ora) <= 1e-4 * np.linalg.norm(g_ora) + np.linalg.norm(amb)

@@ -99,3 +99,28 @@ def test_regulariser_requires_grid_and_adam():
     gs2, arr2 = device_inputs(w2)
     with pytest.raises(_lib.GpairError):
         _lib.Solver(gs2, arr2, _lib.StepParams(rule=_lib.RULE_GD_LINESEARCH, npc=0, vcr_lambda=1e-3))
+
+
+def test_paper_scale_gradient_at_sampled_voxels():
+    """The benchmark's 256 x 256 x 128 volume (16384 tiles, visited in permuted order).  The
+    gradient at a voxel depends on x within two voxels per axis, so the oracle evaluates it on the
+    crop of +-3 voxels around each sample, which is flush with the volume where it meets a face;
+    the samples include faces, edges and corners."""
+    nz, ny, nx = 128, 256, 256
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0.1, 1.0, (nz, ny, nx)).astype(np.float32)
+    beta, lam = 0.5, 1.0
+    xt = torch.as_tensor(x, device="cuda")
+    gt = torch.zeros_like(xt)
+    _lib.gpair_vcr(xt, (nz, ny, nx), beta, 1e-8, lam, gt)
+    g = gt.cpu().numpy()
+    pts = [tuple(int(rng.integers(0, n)) for n in (nz, ny, nx)) for _ in range(60)]
+    pts += [(0, 5, 7), (nz - 1, 100, 3), (50, 0, 200), (60, ny - 1, 1), (10, 20, 0), (11, 21, nx - 1),
+            (0, 0, 0), (nz - 1, ny - 1, nx - 1), (0, ny - 1, 17), (nz - 1, 0, nx - 1), (64, 128, 31), (64, 3, 32)]
+    got, ref = [], []
+    for p in pts:
+        sl = tuple(slice(max(c - 3, 0), min(c + 4, n)) for c, n in zip(p, (nz, ny, nx)))
+        _, gc = vcr.value_and_grad(x[sl].astype(np.float64), beta)
+        ref.append(lam * gc[tuple(c - s.start for c, s in zip(p, sl))])
+        got.append(g[p])
+    assert rel_l2(np.array(got), np.array(ref)) < 1e-5
