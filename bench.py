@@ -63,7 +63,8 @@ def parse():
     p.add_argument("--workload", default="paper", choices=["paper", "mid", "tiny"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sensors", type=int, default=32)
-    p.add_argument("--no-assa", action="store_true", help="skip timing the paper's ASSA operator and the regulariser")
+    p.add_argument("--no-assa", action="store_true",
+                   help="skip timing the paper's ASSA operator, the regulariser, voxelization and the image metrics")
     return p.parse_args()
 
 
@@ -422,6 +423,45 @@ def main():
                "includes": "vcr_fused_kernel (fields in shared memory + transposed-stencil gradient + FP64 "
                            "block partials); no host sync"}
 
+    # ---- voxelization of the image (Eq. 2 sampled on the lattice: three separable gather passes) and
+    # the image metrics (MSE, PSNR, SSIM of the iterate against the phantom): HBM-bound passes
+    vox = met = None
+    if not args.no_assa:
+        x_img = solver.gpair_solver_image()
+        gxi = _lib.Gaussians(A=x_img, grid=grid)
+        vol = torch.empty(w.M, device=dev)
+        for _ in range(2):
+            _lib.gpair_voxelize(gxi, grid, 3.0, vol)
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            _lib.gpair_voxelize(gxi, grid, 3.0, vol)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        xms = v0.elapsed_time(v1) / args.steps
+        xbytes = 8.0 * w.M      # amplitudes in, volume out
+        vox = {"ms": xms, "alg_bytes": xbytes, "achieved_GBs": xbytes / (xms / 1e3) / 1e9, "peak_GBs": HBM_GBS,
+               "frac": xbytes / (xms / 1e3) / 1e9 / HBM_GBS,
+               "includes": "gpair_voxelize, lattice case: three separable passes (24 B per voxel moved)"}
+        dims = (g.nz, g.ny, g.nx)
+        rng_max = float(A_true.max())
+        vals, times = None, []
+        for it in range(2 + args.steps):
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            vals = _lib.gpair_image_metrics(x_img, A_true, dims, 7, rng_max)   # synchronises
+            m1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                times.append(m0.elapsed_time(m1))
+        mms = statistics.median(times)
+        mbytes = 8.0 * w.M      # both volumes read once
+        met = {"ms": mms, "alg_bytes": mbytes, "achieved_GBs": mbytes / (mms / 1e3) / 1e9, "peak_GBs": HBM_GBS,
+               "frac": mbytes / (mms / 1e3) / 1e9 / HBM_GBS, "values": vals, "window": 7,
+               "includes": "gpair_image_metrics on the volume: FP64 MSE, separable box sums, SSIM map, "
+                           "FP64 mean, result copied to the host"}
+
     # the two pipes' rates measured on this device right after the timed work (FFMA and ex2 chains)
     pipe_peaks = {"fp32": _lib.gpair_pipe_peak(_lib.PIPE_FP32) / 1e12, "mufu": _lib.gpair_pipe_peak(_lib.PIPE_MUFU) / 1e12,
                   "unit": "T lane-ops/s", "method": "gpair_pipe_peak: 8 dependent-chain FFMA / ex2.approx streams per "
@@ -481,7 +521,8 @@ def main():
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
                               "step_device": step_ms / max(nrec, 1)},
-                "roofline": roofline, "assa": assa, "vcr": vcr, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "assa": assa, "vcr": vcr, "voxelize": vox, "metrics": met,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -34,6 +34,10 @@ cudaError_t launch_zmap(const float* vol, int nx, int ny, int nz, float* out, cu
 size_t ssim_scratch_bytes(int64_t M);
 cudaError_t launch_ssim_sum(const float* x, const float* y, int nx, int ny, int nz, int win, float range, void* scratch,
                             double* out, cudaStream_t st);
+cudaError_t launch_metrics_march(const float* x, const float* y, int nx, int ny, int nz, int win, float range,
+                                 double* partial, double* res, cudaStream_t st);
+size_t ssim_march_partial_doubles();
+int metrics_march_pmax();
 cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, double* partial,
                        double* value_out, float* g, cudaStream_t st);
 cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
@@ -669,19 +673,28 @@ gpair_status gpair_image_metrics(const float* x, const float* ref, int nx, int n
         return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t M = (int64_t)nx * ny * nz;
+    const int p = (win - 1) / 2;
+    // one fused pass for windows up to 15 (res[0] = sum (x - ref)^2, res[2] = sum of SSIM), else the
+    // FP64 reduction and the per-axis box passes through 10 M floats of scratch volumes
+    const bool fused = p <= metrics_march_pmax();
+    const size_t sbytes = fused ? 0 : align256(ssim_scratch_bytes(M));
+    const size_t npart = std::max(2 * (size_t)red_blocks(), ssim_march_partial_doubles());
     void* scratch = nullptr;
-    const size_t sbytes = align256(ssim_scratch_bytes(M));
-    gpair_status s = get_scratch(st, sbytes + sizeof(double) * (2 * (size_t)red_blocks() + 4), &scratch, nullptr);
+    gpair_status s = get_scratch(st, sbytes + sizeof(double) * (npart + 4), &scratch, nullptr);
     if (s != GPAIR_OK) return s;
     double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + sbytes);
-    double* res = partial + 2 * red_blocks();
-    cudaError_t e = launch_reduce2(x, ref, nullptr, M, partial, res, st);          // res[0] = sum (x - ref)^2
-    if (e == cudaSuccess) e = launch_ssim_sum(x, ref, nx, ny, nz, win, data_range, scratch, res + 2, st);
+    double* res = partial + npart;
+    cudaError_t e;
+    if (fused) {
+        e = launch_metrics_march(x, ref, nx, ny, nz, win, data_range, partial, res, st);
+    } else {
+        e = launch_reduce2(x, ref, nullptr, M, partial, res, st);
+        if (e == cudaSuccess) e = launch_ssim_sum(x, ref, nx, ny, nz, win, data_range, scratch, res + 2, st);
+    }
     if (e != cudaSuccess) return cuda_status(e);
     double h[3];
     if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
-    const int p = (win - 1) / 2;
     const double inner = (double)(nx - 2 * p) * (ny - 2 * p) * (nz > 1 ? nz - 2 * p : 1);
     out[0] = h[0] / (double)M;
     out[1] = 10.0 * std::log10((double)data_range * data_range / out[0]);

@@ -3,8 +3,9 @@
 // The paper gives no formulas; the common definitions are used: SSIM (Wang et al., 2004) with a
 // uniform window of `win` samples per axis, sample (N / (N - 1)) variances and covariance,
 // C1 = (0.01 R)^2, C2 = (0.03 R)^2 for the data range R, averaged over the positions whose window
-// lies inside the image.  The local sums are separable box filters (x, then y, then z), each pass
-// one coalesced read and write of five fields (x, y, x^2, y^2, x y); HBM-bound.
+// lies inside the image.  The local sums are separable box filters (x, then y, then z) of five
+// fields (x, y, x^2, y^2, x y): fused in shared memory for windows up to 15 (ssim_march_kernel,
+// which also sums the squared differences), else one coalesced pass per axis through device memory.
 #include "gpair_internal.cuh"
 
 namespace gp {
@@ -95,6 +96,172 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
         for (int k = 0; k < n; ++k) s += partial[k];    // fixed order
         *out = s;
     }
+}
+
+// Fused MSE + SSIM, marching along z.  A CTA owns a column of SS_TX x SS_TY output positions and
+// a chunk of SS_ZC planes.  Per input plane it stages x and y with a p-voxel halo in x and y,
+// box-sums the five fields along x (shared memory), then along y for its own positions, and keeps
+// the last 2 pz + 1 such planes in a per-thread ring; an output plane's z box sum adds the ring
+// in plane order.  The summation order per position is that of the separable passes above (x, y,
+// then z), so every position's SSIM is the same FP32 value; only x and y cross HBM.  Per-thread
+// sums of (x - y)^2 over the CTA's own voxels and of SSIM over its interior positions are
+// compensated FP32, then FP64 per CTA: partial[2 b] and partial[2 b + 1].
+constexpr int SS_TX = 32, SS_TY = 8, SS_ZC = 16, SS_PMAX = 7;
+// staged entries per thread: (SS_TY + 2 p)(SS_TX + 2 p) <= 22 * 46 = 1012 <= 4 * 256
+constexpr int SS_STAGE = ((SS_TY + 2 * SS_PMAX) * (SS_TX + 2 * SS_PMAX) + 255) / 256;
+static_assert(SS_TX * SS_TY == MET_THREADS, "one thread per output column position");
+
+__host__ __device__ __forceinline__ size_t ssim_march_floats(int p, int pz) {
+    return (size_t)2 * (SS_TY + 2 * p) * (SS_TX + 2 * p) + (size_t)5 * (SS_TY + 2 * p) * SS_TX +
+           (size_t)(2 * pz + 1) * 5 * SS_TY * SS_TX;
+}
+
+__global__ void __launch_bounds__(MET_THREADS)
+ssim_march_kernel(const float* __restrict__ x, const float* __restrict__ y, int nx, int ny, int nz, int p, int pz,
+                  float invN, float cov, float C1, float C2, double* __restrict__ partial) {
+    extern __shared__ float ssm[];
+    __shared__ double red[2][MET_THREADS / 32];
+    const int SW = SS_TX + 2 * p, SH = SS_TY + 2 * p, R = 2 * pz + 1;
+    float* sa = ssm;                              // [SH][SW]
+    float* sb = sa + SH * SW;                     // [SH][SW]
+    float* xb = sb + SH * SW;                     // [5][SH][SS_TX]
+    float* ring = xb + 5 * SH * SS_TX;            // [R][5][SS_TY][SS_TX]
+    const int tx = threadIdx.x % SS_TX, ty = threadIdx.x / SS_TX;
+    const int ncx = (nx + SS_TX - 1) / SS_TX, ncy = (ny + SS_TY - 1) / SS_TY, ncz = (nz + SS_ZC - 1) / SS_ZC;
+    const int nitems = ncx * ncy * ncz;
+    KahanF ksq, kss;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int cx = item % ncx, cy = (item / ncx) % ncy, cz = item / (ncx * ncy);
+        const int X0 = cx * SS_TX, Y0 = cy * SS_TY, Z0 = cz * SS_ZC, Z1 = min(Z0 + SS_ZC, nz);
+        const int gx = X0 + tx, gy = Y0 + ty;
+        const bool own_xy = gx < nx && gy < ny;
+        const bool in_xy = gx >= p && gx < nx - p && gy >= p && gy < ny - p;
+        const int zlo = max(Z0 - pz, 0), zhi = min(Z1 - 1 + pz, nz - 1);
+        // this thread's staging entries q = threadIdx.x + k MET_THREADS (k < SS_STAGE), loaded one
+        // plane ahead into registers so that the loads overlap the previous plane's sums
+        float pa[SS_STAGE], pb[SS_STAGE];
+        auto load_plane = [&](int zi) {
+            const float* xp = x + (int64_t)zi * ny * nx;
+            const float* yp = y + (int64_t)zi * ny * nx;
+#pragma unroll
+            for (int k = 0; k < SS_STAGE; ++k) {
+                const int q = threadIdx.x + k * MET_THREADS;
+                const int r = q / SW, c = q - r * SW;
+                const int ix = X0 - p + c, iy = Y0 - p + r;
+                const bool ok = q < SH * SW && ix >= 0 && ix < nx && iy >= 0 && iy < ny;
+                const int64_t o = (int64_t)iy * nx + ix;
+                pa[k] = ok ? __ldg(xp + o) : 0.f;
+                pb[k] = ok ? __ldg(yp + o) : 0.f;
+            }
+        };
+        load_plane(zlo);
+        for (int zi = zlo; zi <= zhi; ++zi) {
+            __syncthreads();   // the previous plane's readers of sa, sb and xb are done
+#pragma unroll
+            for (int k = 0; k < SS_STAGE; ++k) {
+                const int q = threadIdx.x + k * MET_THREADS;
+                if (q < SH * SW) {
+                    sa[q] = pa[k];
+                    sb[q] = pb[k];
+                }
+            }
+            if (zi < zhi) load_plane(zi + 1);
+            __syncthreads();
+            if (own_xy && zi >= Z0 && zi < Z1) {
+                const float d = sa[(ty + p) * SW + tx + p] - sb[(ty + p) * SW + tx + p];
+                ksq.add(d * d);
+            }
+            for (int q = threadIdx.x; q < SH * SS_TX; q += MET_THREADS) {   // box along x
+                const int r = q / SS_TX, c = q - r * SS_TX;
+                const float* ra = sa + r * SW + c;
+                const float* rb = sb + r * SW + c;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+                for (int d = 0; d <= 2 * p; ++d) {
+                    const float u = ra[d], v = rb[d];
+                    s0 += u; s1 += v; s2 = fmaf(u, u, s2); s3 = fmaf(v, v, s3); s4 = fmaf(u, v, s4);
+                }
+                xb[q] = s0; xb[SH * SS_TX + q] = s1; xb[2 * SH * SS_TX + q] = s2; xb[3 * SH * SS_TX + q] = s3;
+                xb[4 * SH * SS_TX + q] = s4;
+            }
+            __syncthreads();
+            float* rslot = ring + (size_t)(zi % R) * 5 * SS_TY * SS_TX + ty * SS_TX + tx;
+            for (int f = 0; f < 5; ++f) {                                      // box along y (own position)
+                const float* col = xb + (size_t)f * SH * SS_TX + ty * SS_TX + tx;
+                float s = 0.f;
+                for (int d = 0; d <= 2 * p; ++d) s += col[d * SS_TX];
+                rslot[f * SS_TY * SS_TX] = s;
+            }
+            // output plane zi - pz, once its 2 pz + 1 planes are in the ring (this thread's own entries)
+            const int zo = zi - pz;
+            if (in_xy && zo >= Z0 && zo < Z1 && zo >= pz && zo < nz - pz) {
+                float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int zz = zo - pz; zz <= zo + pz; ++zz) {
+                    const float* slot = ring + (size_t)(zz % R) * 5 * SS_TY * SS_TX + ty * SS_TX + tx;
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) S[f] += slot[f * SS_TY * SS_TX];
+                }
+                const float mx = S[0] * invN, my = S[1] * invN;
+                const float sxx = cov * (S[2] * invN - mx * mx);
+                const float syy = cov * (S[3] * invN - my * my);
+                const float sxy = cov * (S[4] * invN - mx * my);
+                kss.add(((2.f * mx * my + C1) * (2.f * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2)));
+            }
+        }
+    }
+    double a = (double)ksq.s - (double)ksq.c, b = (double)kss.s - (double)kss.c;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa2 = 0.0, sb2 = 0.0;
+        for (int k = 0; k < MET_THREADS / 32; ++k) {
+            sa2 += red[0][k];
+            sb2 += red[1][k];
+        }
+        partial[2 * blockIdx.x] = sa2;
+        partial[2 * blockIdx.x + 1] = sb2;
+    }
+}
+
+// res[0] = sum (x - ref)^2 over all voxels, res[2] = sum of SSIM over the interior positions, in
+// fixed CTA order.
+__global__ void ssim_march_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ res) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < n; ++k) {
+            a += partial[2 * k];
+            b += partial[2 * k + 1];
+        }
+        res[0] = a;
+        res[2] = b;
+    }
+}
+
+size_t ssim_march_partial_doubles() { return 2 * (size_t)MET_BLOCKS; }
+int metrics_march_pmax() { return SS_PMAX; }
+
+// cudaErrorNotSupported when the window is wider than the fused kernel handles (caller falls back).
+cudaError_t launch_metrics_march(const float* x, const float* y, int nx, int ny, int nz, int win, float range,
+                                 double* partial, double* res, cudaStream_t st) {
+    const int p = (win - 1) / 2, pz = nz > 1 ? p : 0;
+    if (p > SS_PMAX) return cudaErrorNotSupported;
+    const double N = nz > 1 ? (double)win * win * win : (double)win * win;
+    const size_t sm = ssim_march_floats(p, pz) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(ssim_march_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const float C1 = (0.01f * range) * (0.01f * range), C2 = (0.03f * range) * (0.03f * range);
+    ssim_march_kernel<<<MET_BLOCKS, MET_THREADS, sm, st>>>(x, y, nx, ny, nz, p, pz, (float)(1.0 / N),
+                                                           (float)(N / (N - 1.0)), C1, C2, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ssim_march_finish_kernel<<<1, 32, 0, st>>>(partial, MET_BLOCKS, res);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zmap(const float* vol, int nx, int ny, int nz, float* out, cudaStream_t st) {

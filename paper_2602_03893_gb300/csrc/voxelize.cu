@@ -16,22 +16,56 @@ struct Taps {
     float t[2 * VOX_MAXTAP + 1];
 };
 
-// out = in convolved with taps along one axis (stride s, length n along that axis).
-__global__ void vox_pass_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
-                                int axis, Taps taps) {
-    const int64_t total = (int64_t)nx * ny * nz;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((int64_t)nx * ny));
-        int c, n;
-        int64_t stride;
-        if (axis == 0) { c = ix; n = nx; stride = 1; }
-        else if (axis == 1) { c = iy; n = ny; stride = nx; }
-        else { c = iz; n = nz; stride = (int64_t)nx * ny; }
-        const int lo = max(-taps.mm, -c), hi = min(taps.mm, n - 1 - c);
-        float acc = 0.f;
-        for (int m = lo; m <= hi; ++m) acc = fmaf(taps.t[m + taps.mm], in[v + m * stride], acc);
-        out[v] = acc;
-    }
+// out = in convolved with taps along one axis.  Threads run along x, blocks over (y, z) rows,
+// so no voxel index is divided and every tap's loads are coalesced across the warp.
+constexpr int VOX_THREADS = 256;
+template <int AXIS>
+__global__ void __launch_bounds__(VOX_THREADS)
+vox_pass_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz, Taps taps) {
+    const int ix = blockIdx.x * VOX_THREADS + threadIdx.x;
+    if (ix >= nx) return;
+    const int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny);
+    for (int iz = blockIdx.z; iz < nz; iz += gridDim.z)
+        for (int iy = blockIdx.y; iy < ny; iy += gridDim.y) {
+            const int64_t v = ((int64_t)iz * ny + iy) * nx + ix;
+            const int c = AXIS == 0 ? ix : (AXIS == 1 ? iy : iz), n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
+            const int lo = max(-taps.mm, -c), hi = min(taps.mm, n - 1 - c);
+            float acc = 0.f;
+            for (int m = lo; m <= hi; ++m) acc = fmaf(taps.t[m + taps.mm], __ldg(in + v + m * stride), acc);
+            out[v] = acc;
+        }
+}
+
+// The same pass with the tap count fixed at compile time: the 2 MM + 1 loads of a voxel issue
+// together (out-of-volume taps load nothing and add fmaf(t, 0, acc) = acc, so the sum is the
+// one above, term for term).
+template <int AXIS, int MM>
+__global__ void __launch_bounds__(VOX_THREADS)
+vox_pass_fixed_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz, Taps taps) {
+    const int ix = blockIdx.x * VOX_THREADS + threadIdx.x;
+    if (ix >= nx) return;
+    const int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny);
+    for (int iz = blockIdx.z; iz < nz; iz += gridDim.z)
+        for (int iy = blockIdx.y; iy < ny; iy += gridDim.y) {
+            const int64_t v = ((int64_t)iz * ny + iy) * nx + ix;
+            const int c = AXIS == 0 ? ix : (AXIS == 1 ? iy : iz), n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
+            float val[2 * MM + 1];
+#pragma unroll
+            for (int m = -MM; m <= MM; ++m)
+                val[m + MM] = (unsigned)(c + m) < (unsigned)n ? __ldg(in + v + m * stride) : 0.f;
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m <= 2 * MM; ++m) acc = fmaf(taps.t[m], val[m], acc);
+            out[v] = acc;
+        }
+}
+
+template <int MM>
+static void vox_passes_fixed(const float* A, float* vol, float* tmp, const gpair_grid& og, const Taps& taps,
+                             dim3 grid, cudaStream_t st) {
+    vox_pass_fixed_kernel<0, MM><<<grid, VOX_THREADS, 0, st>>>(A, vol, og.nx, og.ny, og.nz, taps);
+    vox_pass_fixed_kernel<1, MM><<<grid, VOX_THREADS, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, taps);
+    vox_pass_fixed_kernel<2, MM><<<grid, VOX_THREADS, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, taps);
 }
 
 __global__ void zero_kernel(float* p, int64_t n) {
@@ -100,9 +134,20 @@ cudaError_t launch_voxelize(const GaussDev& g, const gpair_grid& og, float k, fl
             double r = m * (double)g.h;
             taps.t[m + mm] = (float)exp(-r * r / (2.0 * (double)g.sigma * g.sigma));
         }
-        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(g.A, vol, og.nx, og.ny, og.nz, 0, taps);
-        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, 1, taps);
-        vox_pass_kernel<<<vox_blocks(nv), 256, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, 2, taps);
+        const dim3 grid((og.nx + VOX_THREADS - 1) / VOX_THREADS, og.ny < 65535 ? og.ny : 65535,
+                        og.nz < 65535 ? og.nz : 65535);
+        switch (mm) {
+            case 1: vox_passes_fixed<1>(g.A, vol, tmp, og, taps, grid, st); break;
+            case 2: vox_passes_fixed<2>(g.A, vol, tmp, og, taps, grid, st); break;
+            case 3: vox_passes_fixed<3>(g.A, vol, tmp, og, taps, grid, st); break;
+            case 4: vox_passes_fixed<4>(g.A, vol, tmp, og, taps, grid, st); break;
+            case 5: vox_passes_fixed<5>(g.A, vol, tmp, og, taps, grid, st); break;
+            case 6: vox_passes_fixed<6>(g.A, vol, tmp, og, taps, grid, st); break;
+            default:
+                vox_pass_kernel<0><<<grid, VOX_THREADS, 0, st>>>(g.A, vol, og.nx, og.ny, og.nz, taps);
+                vox_pass_kernel<1><<<grid, VOX_THREADS, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, taps);
+                vox_pass_kernel<2><<<grid, VOX_THREADS, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, taps);
+        }
         return cudaGetLastError();
     }
     zero_kernel<<<vox_blocks(nv), 256, 0, st>>>(vol, nv);

@@ -12,7 +12,10 @@ from paper_2602_03893_gb300 import _lib
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dims,win", [((20, 24, 28), 7), ((1, 50, 61), 7), ((9, 11, 13), 3), ((7, 7, 7), 7)])
+# windows up to 15 take the fused pass (ragged column tiles of 32 x 8 and z chunks of 16 below);
+# 17 takes the per-axis passes through device memory
+@pytest.mark.parametrize("dims,win", [((20, 24, 28), 7), ((1, 50, 61), 7), ((9, 11, 13), 3), ((7, 7, 7), 7),
+                                      ((37, 45, 70), 7), ((1, 33, 65), 15), ((17, 18, 40), 15), ((19, 20, 21), 17)])
 def test_metrics_against_oracle(dims, win):
     rng = np.random.default_rng(sum(dims))
     ref = rng.uniform(0, 1, dims).astype(np.float32)
@@ -47,3 +50,16 @@ def test_identical_images_and_rejections():
         _lib.gpair_image_metrics(x, x, (8, 9, 10), 4)            # even window
     with pytest.raises(_lib.GpairError):
         _lib.gpair_image_metrics(x[:5].contiguous(), x[:5].contiguous(), (5, 9, 10), 7)   # z shorter than the window
+
+
+def test_paper_scale_volume():
+    """The benchmark's 256 x 256 x 128 volume (2048 column-chunk items over the persistent CTAs)."""
+    dims = (128, 256, 256)
+    rng = np.random.default_rng(41)
+    ref = rng.uniform(0, 1, dims).astype(np.float32)
+    x = np.clip(ref + rng.normal(0, 0.05, dims), 0, 1).astype(np.float32)
+    got = _lib.gpair_image_metrics(torch.as_tensor(x, device="cuda"), torch.as_tensor(ref, device="cuda"), dims, 7)
+    xd, rd = x.astype(np.float64), ref.astype(np.float64)
+    exp_mse = metrics.mse(xd, rd)
+    assert abs(got["mse"] - exp_mse) <= 1e-6 * exp_mse
+    assert abs(got["ssim"] - metrics.ssim(xd, rd, win=7)) <= 1e-5
