@@ -159,3 +159,41 @@ def test_bounded_wait_times_out_and_context_survives():
     with pytest.raises(_lib.GpairError):
         _lib.gpair_wait_selftest(0)                         # rejected on the host, nothing launched
 
+
+
+def test_paper_scale_first_step_in_the_benchmark_configuration():
+    """gpair_step on the benchmark's problem (8.4 M Gaussians, 1024 x 4096 data) from z = 0.
+    With NPC, x0 = eps^2 ~ 1e-16, so y0 ~ 0, the entering loss is |b|^2 / N, and the latent
+    gradient is g_z = 2 eps F^T (-2 b / N) to relative 1e-12.  The oracle computes it for 2000
+    sampled Gaussians and applies its own Adam (first step, bias-corrected: close to -eta sign(g_z),
+    less by the fraction adam_eps / |g_z|).  Entries are compared where |g_z| is at least 1e-3 of
+    the sample's RMS, where the GPU's relative 1e-4 gradient error changes the step by < 1e-4."""
+    w = synth.paper_scale(3)
+    rng = np.random.default_rng(51)
+    b = rng.normal(size=(w.Nd, w.Nt)).astype(np.float32)
+    eta = 0.02
+    p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, npc_eps=1e-8, eta_max=eta, eta_min=0.0, T0=10, T_mult=1.0,
+                        adam_eps=1e-20)
+    gs, arr = device_inputs(w)
+    s = _lib.Solver(gs, arr, p)
+    bt = torch.as_tensor(b, device="cuda")
+    loss0, resid0 = s.gpair_step(bt)
+    z1, _, _, t = s.gpair_solver_get_state()
+    z1 = z1.cpu().numpy()
+    s.close()
+    N = w.Nd * w.Nt
+    bb = float(np.sum(b.astype(np.float64) ** 2))
+    assert t == 1
+    assert abs(loss0 - bb / N) <= 1e-6 * bb / N
+    assert abs(resid0 - np.sqrt(bb)) <= 1e-6 * np.sqrt(bb)
+    idx = np.sort(rng.choice(w.M, 2000, replace=False))
+    G = oracle_gaussians(w, A=np.ones(w.M, np.float32))
+    Gs = oracle.Gaussians(G.c[idx], G.sigma[idx], G.A[idx])
+    gx = oracle.adjoint(Gs, w.sensors, w.v, w.fs, w.t0, w.Nt, -2.0 * b.astype(np.float64) / N, k=w.k)["A"]
+    gz = np.ascontiguousarray(gx * 2.0 * (0.0 + 1e-8))
+    z, m, v = np.zeros(gz.size), np.zeros(gz.size), np.zeros(gz.size)
+    oracle.adam(z, m, v, gz, 1, oracle.cawr(0, eta, 0.0, 10), eps=1e-20)
+    sure = np.abs(gz) >= 1e-3 * np.sqrt(np.mean(gz * gz))
+    assert sure.sum() > 1500
+    assert np.all(np.abs(np.abs(z[sure]) - eta) < 0.05 * eta)
+    np.testing.assert_allclose(z1[idx][sure], z[sure], rtol=1e-4, atol=0)
