@@ -60,12 +60,56 @@ vox_pass_fixed_kernel(const float* __restrict__ in, float* __restrict__ out, int
         }
 }
 
+// The y or z pass with VOX_RUN consecutive outputs per thread along the pass axis: they share
+// their taps' inputs, so a thread loads VOX_RUN + 2 MM values instead of VOX_RUN (2 MM + 1).
+// Each output's sum is the one above, term for term.
+constexpr int VOX_RUN = 4;
+template <int AXIS, int MM>
+__global__ void __launch_bounds__(VOX_THREADS)
+vox_pass_run_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz, Taps taps) {
+    static_assert(AXIS == 1 || AXIS == 2, "runs along y or z");
+    const int ix = blockIdx.x * VOX_THREADS + threadIdx.x;
+    if (ix >= nx) return;
+    const int n = AXIS == 1 ? ny : nz;
+    const int nruns = (n + VOX_RUN - 1) / VOX_RUN;
+    const int64_t stride = AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny;
+    // blockIdx.y runs over (run, other axis) pairs, blockIdx.z over the rest when they exceed 65535
+    for (int64_t u = blockIdx.y + (int64_t)blockIdx.z * gridDim.y; u < (int64_t)nruns * (AXIS == 1 ? nz : ny);
+         u += (int64_t)gridDim.y * gridDim.z) {
+        const int run = (int)(u % nruns), other = (int)(u / nruns);
+        const int c0 = run * VOX_RUN;
+        const int iy = AXIS == 1 ? c0 : other, iz = AXIS == 1 ? other : c0;
+        const int64_t v0 = ((int64_t)iz * ny + iy) * nx + ix;
+        float val[VOX_RUN + 2 * MM];
+#pragma unroll
+        for (int k = 0; k < VOX_RUN + 2 * MM; ++k) {
+            const int c = c0 - MM + k;
+            val[k] = (unsigned)c < (unsigned)n ? __ldg(in + v0 + (int64_t)(k - MM) * stride) : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < VOX_RUN; ++r) {
+            if (c0 + r >= n) break;
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m <= 2 * MM; ++m) acc = fmaf(taps.t[m], val[r + m], acc);
+            out[v0 + (int64_t)r * stride] = acc;
+        }
+    }
+}
+
 template <int MM>
 static void vox_passes_fixed(const float* A, float* vol, float* tmp, const gpair_grid& og, const Taps& taps,
                              dim3 grid, cudaStream_t st) {
     vox_pass_fixed_kernel<0, MM><<<grid, VOX_THREADS, 0, st>>>(A, vol, og.nx, og.ny, og.nz, taps);
-    vox_pass_fixed_kernel<1, MM><<<grid, VOX_THREADS, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, taps);
-    vox_pass_fixed_kernel<2, MM><<<grid, VOX_THREADS, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, taps);
+    const int64_t gy = (int64_t)((og.ny + VOX_RUN - 1) / VOX_RUN) * og.nz;
+    const int64_t gz = (int64_t)((og.nz + VOX_RUN - 1) / VOX_RUN) * og.ny;
+    auto rgrid = [&](int64_t units) {
+        const unsigned y = (unsigned)(units < 65535 ? units : 65535);
+        const int64_t z = (units + y - 1) / y;
+        return dim3(grid.x, y, (unsigned)(z < 65535 ? z : 65535));
+    };
+    vox_pass_run_kernel<1, MM><<<rgrid(gy), VOX_THREADS, 0, st>>>(vol, tmp, og.nx, og.ny, og.nz, taps);
+    vox_pass_run_kernel<2, MM><<<rgrid(gz), VOX_THREADS, 0, st>>>(tmp, vol, og.nx, og.ny, og.nz, taps);
 }
 
 __global__ void zero_kernel(float* p, int64_t n) {
