@@ -420,7 +420,7 @@ def main():
         vbytes = 4.0 * (1 + 2) * w.M
         vcr = {"ms": vms, "alg_bytes": vbytes, "achieved_GBs": vbytes / (vms / 1e3) / 1e9,
                "peak_GBs": HBM_GBS, "frac": vbytes / (vms / 1e3) / 1e9 / HBM_GBS,
-               "includes": "vcr_fused_kernel (fields in shared memory + transposed-stencil gradient + FP64 "
+               "includes": "vcr_march_kernel (fields in shared memory + transposed-stencil gradient + FP64 "
                            "block partials); no host sync"}
 
     # ---- voxelization of the image (Eq. 2 sampled on the lattice: three separable gather passes) and

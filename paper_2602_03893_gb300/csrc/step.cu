@@ -173,23 +173,26 @@ __device__ __forceinline__ int64_t vox(int ix, int iy, int iz, int nx, int ny) {
     return ((int64_t)iz * ny + iy) * nx + ix;
 }
 
-// One fused pass per tile of VT_X x VT_Y x VT_Z voxels.  The CTA stages x on the tile plus two
-// voxels per side (neighbour indices clamped per axis), forms the weighted fields
+// One fused pass marching along z.  A CTA owns a column of VM_TX x VM_TY voxels and a chunk of
+// VM_ZC planes.  Per step it stages one plane of x with two voxels of halo in x and y (neighbour
+// indices clamped per axis: the Neumann reading) into a ring of three planes, forms the weighted
+// fields of the previous plane on the column plus one voxel per side,
 //   F_k = m_k (D_k x) / sqrt(sH + eps)  (k = xx, yy, zz, xy, xz, yz; m = 1, 1, 1, 2, 2, 2),
 //   F_{6+d} = beta (D_d x) / sqrt(sT + eps),
-// sH = sum_{p,q} (D_pq x)^2, sT = sum_d (D_d x)^2, on the tile plus one voxel per side, and adds
-// lam (sum_k D_k^T F_k) to g on the tile.  (D^T F)[j] sums c F[i] over the stencil entries (o, c)
-// and every i whose clamped neighbour i + o is j; inside the volume that is i = j - o, and on a
-// face the clamp adds i = j.  Only x and g cross HBM; the fields stay in shared memory.  The
-// value sum sqrt(sH + eps) + beta sqrt(sT + eps) of the tile's own voxels goes into the CTA's FP64
-// partial.
-constexpr int VT_X = 32, VT_Y = 4, VT_Z = 4;
-constexpr int VX_X = VT_X + 4, VX_Y = VT_Y + 4, VX_Z = VT_Z + 4;    // staged x
-constexpr int VF_X = VT_X + 2, VF_Y = VT_Y + 2, VF_Z = VT_Z + 2;    // staged fields
-constexpr int VF_N = VF_X * VF_Y * VF_Z;
-struct VcrSmem {
-    float xs[VX_Z][VX_Y][VX_X];
-    float F[9][VF_N];
+// sH = sum_{p,q} (D_pq x)^2, sT = sum_d (D_d x)^2, into a ring of three field planes, and adds
+// lam (sum_k D_k^T F_k) to g on the plane before that.  (D^T F)[j] sums c F[i] over the stencil
+// entries (o, c) and every i whose clamped neighbour i + o is j: inside the volume i = j - o, and
+// on a face the clamp adds i = j.  Fields are zero outside the volume, so the gather over j - o
+// needs no masks and a face voxel adds only the terms that take j itself.  Only x and g cross
+// HBM; the fields stay in shared memory.  The value sum sqrt(sH + eps) + beta sqrt(sT + eps) over
+// the CTA's own voxels is compensated FP32 per thread and FP64 per CTA (partial[blockIdx.x]).
+constexpr int VM_TX = 32, VM_TY = 8, VM_ZC = 16;
+constexpr int VM_XW = VM_TX + 4, VM_XH = VM_TY + 4, VM_XN = VM_XW * VM_XH;   // staged x plane
+constexpr int VM_FW = VM_TX + 2, VM_FH = VM_TY + 2, VM_FN = VM_FW * VM_FH;   // field plane
+static_assert(VM_TX * VM_TY == RED_THREADS, "one thread per column position");
+struct VcrMarchSmem {
+    float x[3][VM_XN];
+    float F[3][9][VM_FN];
 };
 
 // Stencil entries of the nine operators: field k, neighbour offset, coefficient.
@@ -209,12 +212,14 @@ __constant__ VcrEntry c_vcr[27] = {
     {8, 0, 0, 1, .5f}, {8, 0, 0, -1, -.5f},
 };
 
-// Extra terms of (sum_k D_k^T F_k)[j] for a voxel on a face of the volume.  Along one axis the
-// preimages of j under the clamped offset o are j - o (when inside) and j itself when j + o falls
-// outside; the gather over j - o with zero fields outside the volume already holds the products
-// of the first kind, so this adds every product that takes j itself along at least one axis.
-__device__ __noinline__ float vcr_fold_terms(const float* F, int jx, int jy, int jz, int nx, int ny, int nz, int X0,
-                                             int Y0, int Z0) {
+// Extra terms of (sum_k D_k^T F_k)[j] for a voxel on an edge or corner of the volume.  Along one
+// axis the preimages of j under the clamped offset o are j - o (when inside) and j itself when
+// j + o falls outside; the gather over j - o with zero fields outside the volume already holds
+// the products of the first kind, so this adds every product that takes j itself along at least
+// one axis.  Fplane[d + 1] is the field plane at z = jz + d ([9][VM_FN] each).
+__device__ __noinline__ float vcr_fold_terms(const float* Fm, const float* F0, const float* Fp, int jx, int jy, int jz,
+                                             int nx, int ny, int nz, int X0, int Y0) {
+    const float* Fplane[3] = {Fm, F0, Fp};
     float s = 0.f;
     for (int e = 0; e < 27; ++e) {
         const VcrEntry E = c_vcr[e];
@@ -227,7 +232,7 @@ __device__ __noinline__ float vcr_fold_terms(const float* F, int jx, int jy, int
             const int px = (m & 1) ? jx : jx - E.ox, py = (m & 2) ? jy : jy - E.oy, pz = (m & 4) ? jz : jz - E.oz;
             // an axis that shifts outside the volume reads a zero field: skip it
             if (px < 0 || px >= nx || py < 0 || py >= ny || pz < 0 || pz >= nz) continue;
-            sum += F[E.k * VF_N + ((pz - Z0 + 1) * VF_Y + (py - Y0 + 1)) * VF_X + (px - X0 + 1)];
+            sum += Fplane[pz - jz + 1][E.k * VM_FN + (py - Y0 + 1) * VM_FW + (px - X0 + 1)];
         }
         s = fmaf(E.c, sum, s);
     }
@@ -236,158 +241,179 @@ __device__ __noinline__ float vcr_fold_terms(const float* F, int jx, int jy, int
 
 template <bool GRAD>
 __global__ void __launch_bounds__(RED_THREADS, 4)
-vcr_fused_kernel(const float* __restrict__ x, int nx, int ny, int nz, float beta, float eps, float lam,
-                 float* __restrict__ g, double* __restrict__ partial, unsigned tile_mul) {
+vcr_march_kernel(const float* __restrict__ x, int nx, int ny, int nz, float beta, float eps, float lam,
+                 float* __restrict__ g, double* __restrict__ partial, unsigned item_mul) {
     extern __shared__ __align__(16) unsigned char vcr_smem[];
-    VcrSmem& S = *reinterpret_cast<VcrSmem*>(vcr_smem);
+    VcrMarchSmem& S = *reinterpret_cast<VcrMarchSmem*>(vcr_smem);
     __shared__ double red[RED_THREADS / 32];
-    __shared__ int tile_org[3];
-    const unsigned ntx = (nx + VT_X - 1) / VT_X, nty = (ny + VT_Y - 1) / VT_Y, ntz = (nz + VT_Z - 1) / VT_Z;
-    const unsigned ntiles = ntx * nty * ntz;                  // < 2^31 (checked on the host)
-    // Tile k of this CTA is t = (blockIdx.x + k gridDim.x) tile_mul mod ntiles, stepped by one add:
-    // tile_mul is coprime to ntiles, so every tile is visited once, and the face tiles, which carry
-    // extra terms, spread over the CTAs instead of one x column staying with a CTA for good.
-    const unsigned step = (unsigned)(((unsigned long long)gridDim.x * tile_mul) % ntiles);
-    unsigned t = (unsigned)(((unsigned long long)blockIdx.x * tile_mul) % ntiles);
+    const int tx = threadIdx.x % VM_TX, ty = threadIdx.x / VM_TX;
+    const unsigned ncx = (nx + VM_TX - 1) / VM_TX, ncy = (ny + VM_TY - 1) / VM_TY, ncz = (nz + VM_ZC - 1) / VM_ZC;
+    const unsigned nitems = ncx * ncy * ncz;                  // < 2^31 (checked on the host)
+    // Item k of this CTA is (blockIdx.x + k gridDim.x) item_mul mod nitems, stepped by one add:
+    // item_mul is coprime to nitems, so every item is visited once, and the face columns, which
+    // carry extra terms, spread over the CTAs.
+    const unsigned step = (unsigned)(((unsigned long long)gridDim.x * item_mul) % nitems);
+    unsigned it = (unsigned)(((unsigned long long)blockIdx.x * item_mul) % nitems);
     KahanF acc;    // this thread's own voxels; FP64 from the CTA sum on
-    for (unsigned tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const unsigned tx = t % ntx, rest = t / ntx;
-            tile_org[0] = (int)tx * VT_X;
-            tile_org[1] = (int)(rest % nty) * VT_Y;
-            tile_org[2] = (int)(rest / nty) * VT_Z;
-        }
-        t += step;
-        if (t >= ntiles) t -= ntiles;
-        __syncthreads();   // the previous tile's readers are done with S; tile_org is published
-        const int X0 = tile_org[0], Y0 = tile_org[1], Z0 = tile_org[2];
-        for (int q = threadIdx.x; q < VX_X * VX_Y * VX_Z; q += RED_THREADS) {
-            const int a = q % VX_X, b = (q / VX_X) % VX_Y, c = q / (VX_X * VX_Y);
-            const int ix = min(max(X0 - 2 + a, 0), nx - 1), iy = min(max(Y0 - 2 + b, 0), ny - 1),
-                      iz = min(max(Z0 - 2 + c, 0), nz - 1);
-            S.xs[c][b][a] = __ldg(x + vox(ix, iy, iz, nx, ny));
-        }
-        __syncthreads();
-        // fields at the positions of the tile +- 1 that lie in the volume; the staged x entry of a
-        // position (a, b, c) of the field grid is (a + 1, b + 1, c + 1)
-        for (int q = threadIdx.x; q < VF_N; q += RED_THREADS) {
-            const int a = q % VF_X, b = (q / VF_X) % VF_Y, c = q / (VF_X * VF_Y);
-            const int px = X0 - 1 + a, py = Y0 - 1 + b, pz = Z0 - 1 + c;
-            const bool inside = px >= 0 && px < nx && py >= 0 && py < ny && pz >= 0 && pz < nz;
-            const bool own = inside && a >= 1 && a <= VT_X && b >= 1 && b <= VT_Y && c >= 1 && c <= VT_Z;
-            if (!inside) {      // zero fields outside the volume: the interior gather then needs no masks
-                if (GRAD)
+    constexpr int SY = VM_FW;
+    for (unsigned k = blockIdx.x; k < nitems; k += gridDim.x) {
+        const unsigned cx = it % ncx, rest = it / ncx;
+        const int X0 = (int)cx * VM_TX, Y0 = (int)(rest % ncy) * VM_TY, Z0 = (int)(rest / ncy) * VM_ZC;
+        const int Z1 = min(Z0 + VM_ZC, nz);
+        it += step;
+        if (it >= nitems) it -= nitems;
+        const int jx = X0 + tx, jy = Y0 + ty;
+        // this thread's staging entries q = threadIdx.x + u RED_THREADS of a plane, loaded one step
+        // ahead into registers so that the loads overlap the previous step's work
+        constexpr int VM_STAGE = (VM_XN + RED_THREADS - 1) / RED_THREADS;
+        float pre[VM_STAGE];
+        auto load_plane = [&](int zi) {
+            const int zc = min(max(zi, 0), nz - 1);
+            const float* xp = x + (int64_t)zc * ny * nx;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) S.F[k][q] = 0.f;
-                continue;
+            for (int u = 0; u < VM_STAGE; ++u) {
+                const int q = threadIdx.x + u * RED_THREADS;
+                const int a = q % VM_XW, b = q / VM_XW;
+                const int ix = min(max(X0 - 2 + a, 0), nx - 1), iy = min(max(Y0 - 2 + b, 0), ny - 1);
+                pre[u] = q < VM_XN ? __ldg(xp + (int64_t)iy * nx + ix) : 0.f;
             }
-            if (!GRAD && !own) continue;
-            auto at = [&](int dx, int dy, int dz) { return S.xs[c + 1 + dz][b + 1 + dy][a + 1 + dx]; };
-            const float c0 = at(0, 0, 0);
-            const float vxp = at(1, 0, 0), vxm = at(-1, 0, 0);
-            const float vyp = at(0, 1, 0), vym = at(0, -1, 0);
-            const float vzp = at(0, 0, 1), vzm = at(0, 0, -1);
-            const float d1x = 0.5f * (vxp - vxm), d1y = 0.5f * (vyp - vym), d1z = 0.5f * (vzp - vzm);
-            const float hxx = (vxp - c0) + (vxm - c0), hyy = (vyp - c0) + (vym - c0), hzz = (vzp - c0) + (vzm - c0);
-            const float hxy = 0.25f * ((at(1, 1, 0) - at(1, -1, 0)) - (at(-1, 1, 0) - at(-1, -1, 0)));
-            const float hxz = 0.25f * ((at(1, 0, 1) - at(1, 0, -1)) - (at(-1, 0, 1) - at(-1, 0, -1)));
-            const float hyz = 0.25f * ((at(0, 1, 1) - at(0, 1, -1)) - (at(0, -1, 1) - at(0, -1, -1)));
-            const float sH = hxx * hxx + hyy * hyy + hzz * hzz + 2.f * (hxy * hxy + hxz * hxz + hyz * hyz);
-            const float sT = d1x * d1x + d1y * d1y + d1z * d1z;
-            if (GRAD) {
-                const float wH = rsqrtf(sH + eps), wT = beta * rsqrtf(sT + eps);
-                S.F[0][q] = wH * hxx;
-                S.F[1][q] = wH * hyy;
-                S.F[2][q] = wH * hzz;
-                S.F[3][q] = 2.f * wH * hxy;
-                S.F[4][q] = 2.f * wH * hxz;
-                S.F[5][q] = 2.f * wH * hyz;
-                S.F[6][q] = wT * d1x;
-                S.F[7][q] = wT * d1y;
-                S.F[8][q] = wT * d1z;
+        };
+        load_plane(Z0 - 2);
+        // step s stages x plane Z0 - 2 + s, forms the fields of plane Z0 - 3 + s (s >= 2) and the
+        // gradient of plane Z0 - 4 + s (s >= 4)
+        for (int s = 0; Z0 - 4 + s < Z1; ++s) {
+            const int zi = Z0 - 2 + s;
+            __syncthreads();   // the readers of the slots overwritten below are done
+            {
+                float* xs = S.x[s % 3];
+#pragma unroll
+                for (int u = 0; u < VM_STAGE; ++u) {
+                    const int q = threadIdx.x + u * RED_THREADS;
+                    if (q < VM_XN) xs[q] = pre[u];
+                }
             }
-            if (own) acc.add(sqrtf(sH + eps) + beta * sqrtf(sT + eps));
-        }
-        if (!GRAD) continue;
-        __syncthreads();
-        for (int q = threadIdx.x; q < VT_X * VT_Y * VT_Z; q += RED_THREADS) {
-            const int a = q % VT_X, b = (q / VT_X) % VT_Y, c = q / (VT_X * VT_Y);
-            const int jx = X0 + a, jy = Y0 + b, jz = Z0 + c;
-            if (jx >= nx || jy >= ny || jz >= nz) continue;
-            const int f0 = ((c + 1) * VF_Y + (b + 1)) * VF_X + (a + 1);
-            // the entries of c_vcr with i = j - o, written out (zero fields outside the volume)
-            constexpr int SY = VF_X, SZ = VF_X * VF_Y;
-            const float* F0 = S.F[0] + f0;
-            const float* F1 = S.F[1] + f0;
-            const float* F2 = S.F[2] + f0;
-            const float* F3 = S.F[3] + f0;
-            const float* F4 = S.F[4] + f0;
-            const float* F5 = S.F[5] + f0;
-            const float* F6 = S.F[6] + f0;
-            const float* F7 = S.F[7] + f0;
-            const float* F8 = S.F[8] + f0;
-            float s = (F0[-1] + F0[1]) - 2.f * F0[0];
-            s += (F1[-SY] + F1[SY]) - 2.f * F1[0];
-            s += (F2[-SZ] + F2[SZ]) - 2.f * F2[0];
-            s += 0.25f * ((F3[-1 - SY] - F3[-1 + SY]) - (F3[1 - SY] - F3[1 + SY]));
-            s += 0.25f * ((F4[-1 - SZ] - F4[-1 + SZ]) - (F4[1 - SZ] - F4[1 + SZ]));
-            s += 0.25f * ((F5[-SY - SZ] - F5[-SY + SZ]) - (F5[SY - SZ] - F5[SY + SZ]));
-            s += 0.5f * (F6[-1] - F6[1]);
-            s += 0.5f * (F7[-SY] - F7[SY]);
-            s += 0.5f * (F8[-SZ] - F8[SZ]);
-            const int fxs = jx == 0 ? -1 : (jx == nx - 1 ? 1 : 0);   // outward offset on a face, else 0
-            const int fys = jy == 0 ? -1 : (jy == ny - 1 ? 1 : 0);
-            const int fzs = jz == 0 ? -1 : (jz == nz - 1 ? 1 : 0);
-            const int nf = (fxs != 0) + (fys != 0) + (fzs != 0);
-            if (nf == 1 && (fxs ? nx : fys ? ny : nz) > 1) {
-                // one face, axis a with outward offset sg: the entries whose offset along a is sg also
-                // take j itself along a (the other axes shift as inside, zero fields outside)
-                const float sg = 0.25f * (float)(fxs + fys + fzs);
-                if (fxs) s += F0[0] + sg * ((F3[-SY] - F3[SY]) + (F4[-SZ] - F4[SZ]) + 2.f * F6[0]);
-                else if (fys) s += F1[0] + sg * ((F3[-1] - F3[1]) + (F5[-SZ] - F5[SZ]) + 2.f * F7[0]);
-                else s += F2[0] + sg * ((F4[-1] - F4[1]) + (F5[-SY] - F5[SY]) + 2.f * F8[0]);
-            } else if (nf != 0) {
-                s += vcr_fold_terms(S.F[0], jx, jy, jz, nx, ny, nz, X0, Y0, Z0);
+            if (Z0 - 4 + s + 1 < Z1) load_plane(zi + 1);
+            __syncthreads();
+            const int zf = zi - 1;
+            if (s >= 2) {
+                const float* xm = S.x[(s + 1) % 3];     // plane zf - 1
+                const float* x0 = S.x[(s + 2) % 3];     // plane zf
+                const float* xq = S.x[s % 3];           // plane zf + 1
+                float* Fz = &S.F[s % 3][0][0];
+                const bool zin = zf >= 0 && zf < nz;
+                const bool zown = zf >= Z0 && zf < Z1;
+                for (int q = threadIdx.x; q < VM_FN; q += RED_THREADS) {
+                    const int a = q % VM_FW, b = q / VM_FW;
+                    const int px = X0 - 1 + a, py = Y0 - 1 + b;
+                    const bool inside = zin && px >= 0 && px < nx && py >= 0 && py < ny;
+                    const bool own = inside && zown && a >= 1 && a <= VM_TX && b >= 1 && b <= VM_TY;
+                    if (!inside) {
+                        if (GRAD)
+#pragma unroll
+                            for (int f = 0; f < 9; ++f) Fz[f * VM_FN + q] = 0.f;
+                        continue;
+                    }
+                    if (!GRAD && !own) continue;
+                    const int o = (b + 1) * VM_XW + (a + 1);   // the position in the staged planes
+                    const float c0 = x0[o];
+                    const float vxp = x0[o + 1], vxm = x0[o - 1];
+                    const float vyp = x0[o + VM_XW], vym = x0[o - VM_XW];
+                    const float vzp = xq[o], vzm = xm[o];
+                    const float d1x = 0.5f * (vxp - vxm), d1y = 0.5f * (vyp - vym), d1z = 0.5f * (vzp - vzm);
+                    const float hxx = (vxp - c0) + (vxm - c0), hyy = (vyp - c0) + (vym - c0), hzz = (vzp - c0) + (vzm - c0);
+                    const float hxy = 0.25f * ((x0[o + 1 + VM_XW] - x0[o + 1 - VM_XW]) - (x0[o - 1 + VM_XW] - x0[o - 1 - VM_XW]));
+                    const float hxz = 0.25f * ((xq[o + 1] - xm[o + 1]) - (xq[o - 1] - xm[o - 1]));
+                    const float hyz = 0.25f * ((xq[o + VM_XW] - xm[o + VM_XW]) - (xq[o - VM_XW] - xm[o - VM_XW]));
+                    const float sH = hxx * hxx + hyy * hyy + hzz * hzz + 2.f * (hxy * hxy + hxz * hxz + hyz * hyz);
+                    const float sT = d1x * d1x + d1y * d1y + d1z * d1z;
+                    if (GRAD) {
+                        const float wH = rsqrtf(sH + eps), wT = beta * rsqrtf(sT + eps);
+                        Fz[0 * VM_FN + q] = wH * hxx;
+                        Fz[1 * VM_FN + q] = wH * hyy;
+                        Fz[2 * VM_FN + q] = wH * hzz;
+                        Fz[3 * VM_FN + q] = 2.f * wH * hxy;
+                        Fz[4 * VM_FN + q] = 2.f * wH * hxz;
+                        Fz[5 * VM_FN + q] = 2.f * wH * hyz;
+                        Fz[6 * VM_FN + q] = wT * d1x;
+                        Fz[7 * VM_FN + q] = wT * d1y;
+                        Fz[8 * VM_FN + q] = wT * d1z;
+                    }
+                    if (own) acc.add(sqrtf(sH + eps) + beta * sqrtf(sT + eps));
+                }
             }
-            const int64_t j = vox(jx, jy, jz, nx, ny);
-            g[j] = fmaf(lam, s, g[j]);
+            if (!GRAD) continue;
+            __syncthreads();
+            const int jz = zi - 2;
+            if (s >= 4 && jz >= Z0 && jx < nx && jy < ny) {
+                const float* Fm = &S.F[(s + 1) % 3][0][0];    // fields of plane jz - 1
+                const float* F0 = &S.F[(s + 2) % 3][0][0];    // plane jz
+                const float* Fp = &S.F[s % 3][0][0];          // plane jz + 1
+                const int f0 = (ty + 1) * VM_FW + (tx + 1);
+                auto A = [&](const float* P, int f, int d) { return P[f * VM_FN + f0 + d]; };
+                // the entries of c_vcr with i = j - o, written out
+                float sg = (A(F0, 0, -1) + A(F0, 0, 1)) - 2.f * A(F0, 0, 0);
+                sg += (A(F0, 1, -SY) + A(F0, 1, SY)) - 2.f * A(F0, 1, 0);
+                sg += (A(Fm, 2, 0) + A(Fp, 2, 0)) - 2.f * A(F0, 2, 0);
+                sg += 0.25f * ((A(F0, 3, -1 - SY) - A(F0, 3, -1 + SY)) - (A(F0, 3, 1 - SY) - A(F0, 3, 1 + SY)));
+                sg += 0.25f * ((A(Fm, 4, -1) - A(Fp, 4, -1)) - (A(Fm, 4, 1) - A(Fp, 4, 1)));
+                sg += 0.25f * ((A(Fm, 5, -SY) - A(Fp, 5, -SY)) - (A(Fm, 5, SY) - A(Fp, 5, SY)));
+                sg += 0.5f * (A(F0, 6, -1) - A(F0, 6, 1));
+                sg += 0.5f * (A(F0, 7, -SY) - A(F0, 7, SY));
+                sg += 0.5f * (A(Fm, 8, 0) - A(Fp, 8, 0));
+                const int fxs = jx == 0 ? -1 : (jx == nx - 1 ? 1 : 0);   // outward offset on a face, else 0
+                const int fys = jy == 0 ? -1 : (jy == ny - 1 ? 1 : 0);
+                const int fzs = jz == 0 ? -1 : (jz == nz - 1 ? 1 : 0);
+                const int nf = (fxs != 0) + (fys != 0) + (fzs != 0);
+                if (nf == 1 && (fxs ? nx : fys ? ny : nz) > 1) {
+                    // one face, axis a with outward offset: the entries whose offset along a is that
+                    // offset also take j itself along a (the other axes shift as inside)
+                    const float h = 0.25f * (float)(fxs + fys + fzs);
+                    if (fxs) sg += A(F0, 0, 0) + h * ((A(F0, 3, -SY) - A(F0, 3, SY)) + (A(Fm, 4, 0) - A(Fp, 4, 0)) + 2.f * A(F0, 6, 0));
+                    else if (fys) sg += A(F0, 1, 0) + h * ((A(F0, 3, -1) - A(F0, 3, 1)) + (A(Fm, 5, 0) - A(Fp, 5, 0)) + 2.f * A(F0, 7, 0));
+                    else sg += A(F0, 2, 0) + h * ((A(F0, 4, -1) - A(F0, 4, 1)) + (A(F0, 5, -SY) - A(F0, 5, SY)) + 2.f * A(F0, 8, 0));
+                } else if (nf != 0) {
+                    sg += vcr_fold_terms(Fm, F0, Fp, jx, jy, jz, nx, ny, nz, X0, Y0);
+                }
+                const int64_t j = vox(jx, jy, jz, nx, ny);
+                g[j] = fmaf(lam, sg, g[j]);
+            }
         }
     }
     const double tot = block_sum((double)acc.s - (double)acc.c, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-int64_t vcr_tiles(int nx, int ny, int nz) {
-    return (int64_t)((nx + VT_X - 1) / VT_X) * ((ny + VT_Y - 1) / VT_Y) * ((nz + VT_Z - 1) / VT_Z);
+int64_t vcr_items(int nx, int ny, int nz) {
+    return (int64_t)((nx + VM_TX - 1) / VM_TX) * ((ny + VM_TY - 1) / VM_TY) * ((nz + VM_ZC - 1) / VM_ZC);
 }
 
-// Multiplier of the tile permutation: an odd prime that does not divide the tile count.
-unsigned vcr_tile_mul(int nx, int ny, int nz) {
-    const int64_t n = vcr_tiles(nx, ny, nz);
+// Multiplier of the item permutation: an odd prime that does not divide the item count.
+unsigned vcr_item_mul(int nx, int ny, int nz) {
+    const int64_t n = vcr_items(nx, ny, nz);
     const int64_t primes[] = {7919, 7927, 7933, 7937, 7949};
     for (int64_t p : primes)
         if (n % p != 0) return p % n == 0 ? 1u : (unsigned)p;
     return 1u;
 }
 
-size_t vcr_smem_bytes(bool grad) { return grad ? sizeof(VcrSmem) : sizeof(float) * VX_X * VX_Y * VX_Z; }
+size_t vcr_smem_bytes(bool grad) { return grad ? sizeof(VcrMarchSmem) : sizeof(float) * 3 * VM_XN; }
 
 // value_out (device, may be NULL): R_VCR(x) in FP64.  g (may be NULL): g += lam grad R_VCR(x).
 // partial: RED_BLOCKS doubles.
 cudaError_t launch_vcr(const float* x, int nx, int ny, int nz, float beta, float eps, float lam, double* partial,
                        double* value_out, float* g, cudaStream_t st) {
-    if (vcr_tiles(nx, ny, nz) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+    if (vcr_items(nx, ny, nz) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     cudaError_t e;
+    const unsigned mul = vcr_item_mul(nx, ny, nz);
     if (g) {
         const size_t sm = vcr_smem_bytes(true);
-        if ((e = cudaFuncSetAttribute(vcr_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        if ((e = cudaFuncSetAttribute(vcr_march_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
             cudaSuccess)
             return e;
-        vcr_fused_kernel<true><<<RED_BLOCKS, RED_THREADS, sm, st>>>(x, nx, ny, nz, beta, eps, lam, g, partial,
-                                                                    vcr_tile_mul(nx, ny, nz));
+        vcr_march_kernel<true><<<RED_BLOCKS, RED_THREADS, sm, st>>>(x, nx, ny, nz, beta, eps, lam, g, partial, mul);
     } else {
-        vcr_fused_kernel<false><<<RED_BLOCKS, RED_THREADS, vcr_smem_bytes(false), st>>>(
-            x, nx, ny, nz, beta, eps, lam, nullptr, partial, vcr_tile_mul(nx, ny, nz));
+        vcr_march_kernel<false><<<RED_BLOCKS, RED_THREADS, vcr_smem_bytes(false), st>>>(x, nx, ny, nz, beta, eps, lam,
+                                                                                       nullptr, partial, mul);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (value_out) {
