@@ -230,17 +230,29 @@ ssim_march_kernel(const float* __restrict__ x, const float* __restrict__ y, int 
     }
 }
 
-// res[0] = sum (x - ref)^2 over all voxels, res[2] = sum of SSIM over the interior positions, in
-// fixed CTA order.
-__global__ void ssim_march_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ res) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < n; ++k) {
-            a += partial[2 * k];
-            b += partial[2 * k + 1];
+// res[0] = sum (x - ref)^2 over all voxels, res[2] = sum of SSIM over the interior positions: each
+// thread sums a fixed stride of the CTA partials, then a fixed tree (deterministic).
+__global__ void __launch_bounds__(MET_THREADS)
+ssim_march_finish_kernel(const double* __restrict__ partial, int n, double* __restrict__ res) {
+    __shared__ double sa[MET_THREADS], sb[MET_THREADS];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < n; k += MET_THREADS) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = MET_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sa[threadIdx.x] += sa[threadIdx.x + w];
+            sb[threadIdx.x] += sb[threadIdx.x + w];
         }
-        res[0] = a;
-        res[2] = b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        res[0] = sa[0];
+        res[2] = sb[0];
     }
 }
 
@@ -260,7 +272,7 @@ cudaError_t launch_metrics_march(const float* x, const float* y, int nx, int ny,
     ssim_march_kernel<<<MET_BLOCKS, MET_THREADS, sm, st>>>(x, y, nx, ny, nz, p, pz, (float)(1.0 / N),
                                                            (float)(N / (N - 1.0)), C1, C2, partial);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ssim_march_finish_kernel<<<1, 32, 0, st>>>(partial, MET_BLOCKS, res);
+    ssim_march_finish_kernel<<<1, MET_THREADS, 0, st>>>(partial, MET_BLOCKS, res);
     return cudaGetLastError();
 }
 
