@@ -545,7 +545,11 @@ gpair_status gpair_last_device_status(void* stream) {
     return GPAIR_OK;
 }
 
+}  // extern "C"
+
 // ---- the paper's operator (Methods, adaptive supersampling alignment; Algorithm 1) -------------
+// Helpers of the ASSA entry points and of the solver's ASSA path (file-local).
+namespace {
 
 // Grid parameters and the sampled pulse: N_half = ceil(3 sigma / (v / fs)),
 // alpha = max(1, ceil(((N_min - 1) / 2) / N_half)), K = alpha N_half, all in double from the
@@ -608,6 +612,10 @@ gpair_status run_assa_forward(const GaussDev& g, const ArrDev& aa, const AssaTab
     if (e == cudaSuccess) e = launch_slab_reduce(g, aa, part, rows, p.S, p.PL, y, st);
     return cuda_status(e);
 }
+
+}  // namespace
+
+extern "C" {
 
 gpair_status gpair_assa_forward(const gpair_gaussians* gi, const gpair_array* ai, int n_min, float* y, void* stream) {
     GaussDev g;
