@@ -516,7 +516,7 @@ def main():
                            "grid": [g.nx, g.ny, g.nz], "spacing_m": g.h, "sigma_m": g.sigma, "window_k": w.k,
                            "fs_hz": w.fs, "sound_speed": w.v, "step": "Adam + NPC + CAWR, FP64 loss",
                            "l2": "inputs larger than L2: A, z, m, v 33.5 MB each, y and b 16.8 MB each, "
-                                 "slab partials 75 MB",
+                                 "banded slab partial rows 180 MB",
                            "parallelism": f"replicas{world}"},
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
