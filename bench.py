@@ -135,6 +135,18 @@ def profiled_traffic(kernel, src):
     return None
 
 
+L2_MB = 129.0    # GB300 L2
+
+
+def l2_note(w):
+    """How the step's operands compare with L2 (no flush is done between timed steps)."""
+    vol_mb, rec_mb = 4.0 * w.M / 1e6, 4.0 * w.Nd * w.Nt / 1e6
+    step_mb = 5 * vol_mb + 3 * rec_mb     # A-sized z, m, v, x, gradient; y, b and the residual
+    kind = "larger than L2" if step_mb > L2_MB else "SMALLER than L2 (cached between steps)"
+    return (f"operands {kind} ({L2_MB:.0f} MB): {vol_mb:.1f} MB per volume (z, m, v, x, gradient), "
+            f"{rec_mb:.1f} MB per record (y, b, residual), {step_mb:.0f} MB per step without the slab partial rows")
+
+
 class ClockSampler:
     """nvidia-smi sampling of the device's SM clock and throttle reasons every 200 ms."""
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -515,8 +527,7 @@ def main():
                 "config": {"workload": w.name, "gaussians": w.M, "sensors": w.Nd, "samples": w.Nt,
                            "grid": [g.nx, g.ny, g.nz], "spacing_m": g.h, "sigma_m": g.sigma, "window_k": w.k,
                            "fs_hz": w.fs, "sound_speed": w.v, "step": "Adam + NPC + CAWR, FP64 loss",
-                           "l2": "inputs larger than L2: A, z, m, v 33.5 MB each, y and b 16.8 MB each, "
-                                 "banded slab partial rows 180 MB",
+                           "l2": l2_note(w),
                            "parallelism": f"replicas{world}"},
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
