@@ -39,7 +39,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 MUFU_LANES_PER_SM = 32          # MUFU lanes per SM (ex2 measured at ~30 lane-ops / clk / SM)
-LAUNCHES_PER_STEP = 9           # npc, slab info, forward, slab reduce, resid, finish, Q table, adjoint, adam
+LAUNCHES_PER_STEP = 10          # npc, slab info, forward, slab reduce, resid, finish, Q table, adjoint, schedule, adam
 ASSA_NMIN = 25                  # the paper's minimum number of fine samples across the pulse
 
 
@@ -367,6 +367,17 @@ def main():
     e2e = {"value": tw / (e2e_steps * world), "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 4),
            "d2h_bytes_per_step": 8, "loss_last": loss}
 
+    # ---- the same K steps replayed as one CUDA graph (gpair_solver_steps), device time; the first
+    # call captures the graph
+    solver.gpair_solver_steps(b, 1, want_loss=False)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    solver.gpair_solver_steps(b, args.steps, want_loss=False)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, world)
+
     # ---- the paper's own operator (ASSA, Algorithm 1) on the same workload and the solver's image,
     # timed after the IR step; the paper's figures (RTX 5090) are context
     assa = None
@@ -532,6 +543,7 @@ def main():
                 "pair_evals_per_s": 2 * pairs / per_iter, "sample_evals_per_s": 2 * samples / per_iter,
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
                               "step_device": step_ms / max(nrec, 1)},
+                "graph_ms_per_step": graph_ms,
                 "roofline": roofline, "assa": assa, "vcr": vcr, "voxelize": vox, "metrics": met,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}

@@ -180,6 +180,16 @@ void gpair_solver_destroy(gpair_solver* s);
 gpair_status gpair_step(gpair_solver* s, const float* b, double* loss_out, double* resid_out,
                         void* stream);
 
+/* n iterations of gpair_step on the same data b (device [n_sensors][n_samples]), replayed as one
+ * CUDA graph: the step's launches are captured once per (solver, b) on a private stream and the
+ * graph is launched n times on `stream`.  The per-step scalars (CAWR step size, Adam's bias
+ * corrections) live on the device, so every step's launches are identical: the same kernels with
+ * the same arguments as n gpair_step calls.  loss_out / resid_out (host, may be NULL) receive the values of the
+ * iterate entering the last step (the call then synchronises `stream`).  With profiling enabled
+ * the steps run one by one through gpair_step.  GPAIR_ERR_INVALID_ARG for NULL s or b, or n < 0. */
+gpair_status gpair_solver_steps(gpair_solver* s, const float* b, int n, double* loss_out, double* resid_out,
+                                void* stream);
+
 /* Current image x = phi(z) (device [M] float32, written asynchronously). */
 gpair_status gpair_solver_image(gpair_solver* s, float* x_out, void* stream);
 /* Latent z, Adam moments m, v (device [M] each, any may be NULL) and the iteration count:

@@ -26,7 +26,7 @@ OP_EXACT, OP_ASSA = 0, 1          # gpair_step_params.op
 # Symbols declared in include/gpair.h (checked by the CPU test suite).
 EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
-           "gpair_solver_profile", "gpair_solver_timings",
+           "gpair_solver_profile", "gpair_solver_timings", "gpair_solver_steps",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
            "gpair_wait_selftest", "gpair_assa_forward", "gpair_assa_adjoint", "gpair_vcr", "gpair_zmap",
            "gpair_image_metrics", "gpair_pipe_peak", "gpair_version")
@@ -78,6 +78,7 @@ def load(path: str | None = None):
         lib.gpair_solver_destroy.argtypes = [P]
         lib.gpair_solver_destroy.restype = None
         lib.gpair_step.argtypes = [P, P, ctypes.POINTER(c_double), ctypes.POINTER(c_double), P]
+        lib.gpair_solver_steps.argtypes = [P, P, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_double), P]
         lib.gpair_solver_image.argtypes = [P, P, P]
         lib.gpair_solver_get_state.argtypes = [P, P, P, P, ctypes.POINTER(c_int), P]
         lib.gpair_solver_set_state.argtypes = [P, P, P, P, c_int, P]
@@ -372,6 +373,16 @@ class Solver:
         loss, resid = c_double(), c_double()
         _check("gpair_step", lib.gpair_step(self._h, _ptr(b), ctypes.byref(loss) if want_loss else None,
                                             ctypes.byref(resid) if want_loss else None, _stream(stream)))
+        return (loss.value, resid.value) if want_loss else None
+
+    def gpair_solver_steps(self, b: torch.Tensor, n: int, want_loss: bool = True, stream=None):
+        """n steps replayed as one CUDA graph; (loss, resid) of the iterate entering the last one."""
+        lib = load()
+        loss, resid = c_double(), c_double()
+        _check("gpair_solver_steps", lib.gpair_solver_steps(self._h, _ptr(b), int(n),
+                                                            ctypes.byref(loss) if want_loss else None,
+                                                            ctypes.byref(resid) if want_loss else None,
+                                                            _stream(stream)))
         return (loss.value, resid.value) if want_loss else None
 
     def gpair_solver_image(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "gpair_internal.cuh"
+#include "step_sched.cuh"
 
 namespace gp {
 cudaError_t launch_tile_info(const GaussDev& g, TileInfo* ti, cudaStream_t st);
@@ -52,8 +53,10 @@ cudaError_t launch_reduce2(const float* a, const float* b, const float* c, int64
                            cudaStream_t st);
 cudaError_t launch_ls(const float* r, const float* Fg, int64_t n, float* x, const float* g, int64_t M,
                       double* partial, double* nd, cudaStream_t st);
-cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float eta,
-                        float b1, float b2, float inv_c1, float inv_sqrt_c2, float adam_eps, cudaStream_t st);
+cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float b1,
+                        float b2, float adam_eps, const StepSched* sd, cudaStream_t st);
+cudaError_t launch_schedule(const SchedParams& p, StepSched* sd, cudaStream_t st);
+cudaError_t launch_set_step(StepSched* sd, int t, cudaStream_t st);
 int red_blocks();
 bool vox_is_lattice(const GaussDev& g, const gpair_grid& og);
 cudaError_t launch_voxelize(const GaussDev& g, const gpair_grid& og, float k, float* vol, float* tmp, cudaStream_t st);
@@ -758,6 +761,13 @@ struct gpair_solver {
     AssaTable T;
     ArrDev aa;
     float* dconv = nullptr;
+    // Per-step scalars on the device (CAWR step size, Adam bias corrections, the step count).
+    StepSched* sd = nullptr;
+    SchedParams sched{};
+    // gpair_solver_steps: one step captured as a CUDA graph (on a private stream) for data b.
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const float* gb = nullptr;
     // Profiling (gpair_solver_profile): per recorded step six events on the step's stream --
     // step start, forward slab kernel start/end, adjoint kernel start/end, step end.
     bool prof = false;
@@ -766,16 +776,6 @@ struct gpair_solver {
 };
 
 namespace {
-double cawr(int t, const gpair_step_params& p) {
-    // SGDR: periods T0, T0*Tmult, ...; T_cur counts iterations since the last restart.
-    double Tcur = t, Ti = p.T0 > 0 ? p.T0 : 1;
-    if (p.T_mult <= 1.0f) {
-        Tcur = std::fmod(Tcur, Ti);
-    } else {
-        while (Tcur >= Ti) { Tcur -= Ti; Ti *= p.T_mult; }
-    }
-    return p.eta_min + 0.5 * (p.eta_max - p.eta_min) * (1.0 + std::cos(M_PI * Tcur / Ti));
-}
 
 // y = F(S->g with amplitudes S->g.A) on the solver's operator; ev (optional) brackets its main kernel.
 gpair_status solver_forward(gpair_solver* S, float* y, const cudaEvent_t* ev, cudaStream_t st) {
@@ -842,7 +842,8 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
               cudaMalloc(&S->fwd_scratch, S->plan.bytes + (assa ? ASSA_EXTRA_BYTES : 0)) == cudaSuccess &&
               (qbytes == 0 || cudaMalloc(&S->qbuf, qbytes) == cudaSuccess) &&
               (!assa || cudaMalloc(&S->dconv, assa_dconv_bytes(a, S->T)) == cudaSuccess) &&
-              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&S->status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&S->sd, sizeof(StepSched)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         gpair_solver_destroy(S);
@@ -852,6 +853,8 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     cudaMemset(S->m, 0, M * 4);
     cudaMemset(S->v, 0, M * 4);
     cudaMemset(S->status, 0, sizeof(int));
+    cudaMemset(S->sd, 0, sizeof(StepSched));
+    S->sched = SchedParams{prm->eta_max, prm->eta_min, prm->T_mult, prm->beta1, prm->beta2, prm->T0};
     if (cudaDeviceSynchronize() != cudaSuccess) {
         gpair_solver_destroy(S);
         return GPAIR_ERR_CUDA;
@@ -865,7 +868,9 @@ void gpair_solver_destroy(gpair_solver* S) {
     if (!S) return;
     cudaFree(S->z); cudaFree(S->m); cudaFree(S->v); cudaFree(S->x); cudaFree(S->gx);
     cudaFree(S->y); cudaFree(S->delta); cudaFree(S->Fg); cudaFree(S->red);
-    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->dconv);
+    cudaFree(S->fwd_scratch); cudaFree(S->qbuf); cudaFree(S->status); cudaFree(S->dconv); cudaFree(S->sd);
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
+    if (S->cap) cudaStreamDestroy(S->cap);
     for (cudaEvent_t ev : S->evs) cudaEventDestroy(ev);
     delete S;
 }
@@ -894,24 +899,17 @@ gpair_status gpair_solver_timings(gpair_solver* S, double* ms, int* nsteps) {
     return GPAIR_OK;
 }
 
-gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, double* resid_out, void* stream) {
-    if (!S || !b) return GPAIR_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+// The launches of one reconstruction step on st: no host synchronisation, S->t unchanged, and the
+// same launches with the same arguments at every step (so that they can be replayed as a graph).
+gpair_status step_launches(gpair_solver* S, const float* b, const cudaEvent_t* ev, cudaStream_t st) {
     const int64_t M = S->g.M, N = (int64_t)S->a.Nd * S->a.Nt;
     double* partial = S->red;
     double* res = S->red + 2 * red_blocks();
     cudaError_t e;
     gpair_status s;
-    const cudaEvent_t* ev = nullptr;
-    if (S->prof) {
-        while ((int)S->evs.size() < 6 * (S->nrec + 1)) {
-            cudaEvent_t x;
-            if (cudaEventCreate(&x) != cudaSuccess) return GPAIR_ERR_CUDA;
-            S->evs.push_back(x);
-        }
-        ev = &S->evs[6 * S->nrec];
-        if (cudaEventRecord(ev[0], st) != cudaSuccess) return GPAIR_ERR_CUDA;
-    }
     if (S->p.rule == GPAIR_RULE_ADAM) {
         const int npc = S->p.npc != 0;
         if ((e = launch_npc(S->z, S->x, M, npc, S->p.npc_eps, st)) != cudaSuccess) return cuda_status(e);
@@ -923,38 +921,110 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
             (e = launch_vcr(S->x, S->g.nx, S->g.ny, S->g.nz, S->p.vcr_beta, S->p.vcr_eps, S->p.vcr_lambda, partial,
                             res + 4, S->gx, st)) != cudaSuccess)
             return cuda_status(e);
-        const int tt = S->t + 1;
-        const double c1 = 1.0 - std::pow((double)S->p.beta1, tt), c2 = 1.0 - std::pow((double)S->p.beta2, tt);
-        const float eta = (float)cawr(S->t, S->p);
-        if ((e = launch_adam(S->z, S->m, S->v, S->gx, M, npc, S->p.npc_eps, eta, S->p.beta1, S->p.beta2,
-                             (float)(1.0 / c1), (float)(1.0 / std::sqrt(c2)), S->p.adam_eps, st)) != cudaSuccess)
+        // CAWR step size and bias corrections of this step, from the device step count
+        if ((e = launch_schedule(S->sched, S->sd, st)) != cudaSuccess) return cuda_status(e);
+        if ((e = launch_adam(S->z, S->m, S->v, S->gx, M, npc, S->p.npc_eps, S->p.beta1, S->p.beta2, S->p.adam_eps,
+                             S->sd, st)) != cudaSuccess)
             return cuda_status(e);
     } else {
         // steepest descent on x = z with the exact line search alpha = <r, F g> / |F g|^2
         S->g.A = S->z;
-        if ((s = solver_forward(S, S->y, ev ? ev + 1 : nullptr, st)) != GPAIR_OK) return s;
-        if ((e = launch_resid(S->y, b, S->delta, 1.0f, N, partial, res, st)) != cudaSuccess) return cuda_status(e);
-        if ((s = solver_adjoint(S, S->delta, S->gx, ev ? ev + 3 : nullptr, st)) != GPAIR_OK) return s;
+        s = solver_forward(S, S->y, ev ? ev + 1 : nullptr, st);
+        if (s == GPAIR_OK && (e = launch_resid(S->y, b, S->delta, 1.0f, N, partial, res, st)) != cudaSuccess)
+            s = cuda_status(e);
+        if (s == GPAIR_OK) s = solver_adjoint(S, S->delta, S->gx, ev ? ev + 3 : nullptr, st);
         S->g.A = S->gx;
-        if ((s = solver_forward(S, S->Fg, nullptr, st)) != GPAIR_OK) return s;
-        if ((e = launch_ls(S->delta, S->Fg, N, S->z, S->gx, M, partial, res + 2, st)) != cudaSuccess)
-            return cuda_status(e);
+        if (s == GPAIR_OK) s = solver_forward(S, S->Fg, nullptr, st);
+        if (s == GPAIR_OK && (e = launch_ls(S->delta, S->Fg, N, S->z, S->gx, M, partial, res + 2, st)) != cudaSuccess)
+            s = cuda_status(e);
         S->g.A = S->x;
+        if (s != GPAIR_OK) return s;
     }
+    return GPAIR_OK;
+}
+
+// The FP64 loss and residual norm of the iterate that entered the last step (synchronises st).
+gpair_status read_loss(gpair_solver* S, cudaStream_t st, double* loss_out, double* resid_out) {
+    if (!loss_out && !resid_out) return GPAIR_OK;
+    const double N = (double)S->a.Nd * S->a.Nt;
+    const double* res = S->red + 2 * red_blocks();
+    double h[5] = {0, 0, 0, 0, 0};
+    if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    const double reg = S->vcr ? (double)S->p.vcr_lambda * h[4] : 0.0;
+    if (loss_out) *loss_out = h[0] / N + reg;
+    if (resid_out) *resid_out = std::sqrt(h[0]);
+    return GPAIR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, double* resid_out, void* stream) {
+    if (!S || !b) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaEvent_t* ev = nullptr;
+    if (S->prof) {
+        while ((int)S->evs.size() < 6 * (S->nrec + 1)) {
+            cudaEvent_t x;
+            if (cudaEventCreate(&x) != cudaSuccess) return GPAIR_ERR_CUDA;
+            S->evs.push_back(x);
+        }
+        ev = &S->evs[6 * S->nrec];
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    }
+    gpair_status s = step_launches(S, b, ev, st);
+    if (s != GPAIR_OK) return s;
     if (ev) {
         if (cudaEventRecord(ev[5], st) != cudaSuccess) return GPAIR_ERR_CUDA;
         S->nrec += 1;
     }
     S->t += 1;
-    if (loss_out || resid_out) {
-        double h[5] = {0, 0, 0, 0, 0};
-        if (cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GPAIR_ERR_CUDA;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return GPAIR_ERR_CUDA;
-        const double reg = S->vcr ? (double)S->p.vcr_lambda * h[4] : 0.0;
-        if (loss_out) *loss_out = h[0] / (double)N + reg;
-        if (resid_out) *resid_out = std::sqrt(h[0]);
+    return read_loss(S, st, loss_out, resid_out);
+}
+
+gpair_status gpair_solver_steps(gpair_solver* S, const float* b, int n, double* loss_out, double* resid_out,
+                                void* stream) {
+    if (!S || !b || n < 0) return GPAIR_ERR_INVALID_ARG;
+    if (n == 0) return GPAIR_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (S->prof) {   // profiling records events per step: step by step
+        for (int k = 0; k < n; ++k) {
+            const bool last = k == n - 1;
+            const gpair_status s = gpair_step(S, b, last ? loss_out : nullptr, last ? resid_out : nullptr, stream);
+            if (s != GPAIR_OK) return s;
+        }
+        return GPAIR_OK;
     }
-    return GPAIR_OK;
+    if (!S->gexec || S->gb != b) {
+        if (S->gexec) {
+            cudaGraphExecDestroy(S->gexec);
+            S->gexec = nullptr;
+        }
+        if (!S->cap && cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking) != cudaSuccess) return GPAIR_ERR_CUDA;
+        // the capture records the step's launches without running them
+        if (cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GPAIR_ERR_CUDA;
+        const gpair_status s = step_launches(S, b, nullptr, S->cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(S->cap, &graph);
+        if (s != GPAIR_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != GPAIR_OK ? s : GPAIR_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&S->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            S->gexec = nullptr;
+            cudaGetLastError();
+            return GPAIR_ERR_CUDA;
+        }
+        S->gb = b;
+    }
+    for (int k = 0; k < n; ++k)
+        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    S->t += n;
+    return read_loss(S, st, loss_out, resid_out);
 }
 
 gpair_status gpair_solver_image(gpair_solver* S, float* x_out, void* stream) {
@@ -982,6 +1052,7 @@ gpair_status gpair_solver_set_state(gpair_solver* S, const float* z, const float
     if (z && cudaMemcpyAsync(S->z, z, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     if (m && cudaMemcpyAsync(S->m, m, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     if (v && cudaMemcpyAsync(S->v, v, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (launch_set_step(S->sd, t, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     S->t = t;
     return GPAIR_OK;
 }

@@ -4,6 +4,7 @@
 // search step of the steepest-descent variant.  All HBM-bound; FP64 is used only inside the
 // reductions.
 #include "gpair_internal.cuh"
+#include "step_sched.cuh"
 
 namespace gp {
 
@@ -78,9 +79,39 @@ __global__ void finish_kernel(const double* __restrict__ partial, int nblk, int 
 }
 
 // Adam on z with gradient g_x (and the NPC chain rule g_z = g_x * 2 (z + eps)).
+// Per-step scalars of Algorithm 2 on the device, so that a step's launches do not change from one
+// step to the next (and can be replayed as a CUDA graph): the CAWR step size of step t and Adam's
+// bias corrections 1 / (1 - b1^(t+1)), 1 / sqrt(1 - b2^(t+1)).  schedule_kernel advances t.
+__global__ void schedule_kernel(SchedParams p, StepSched* __restrict__ sd) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int t = sd->t;
+    // SGDR: periods T0, T0 T_mult, ...; T_cur counts iterations since the last restart
+    double Tcur = t, Ti = p.T0 > 0 ? p.T0 : 1;
+    if (p.T_mult <= 1.0) {
+        Tcur = fmod(Tcur, Ti);
+    } else {
+        for (int guard = 0; Tcur >= Ti && guard < 4096; ++guard) {   // O(log t) periods
+            Tcur -= Ti;
+            Ti *= p.T_mult;
+        }
+    }
+    const double eta = p.eta_min + 0.5 * (p.eta_max - p.eta_min) * (1.0 + cos(3.141592653589793 * Tcur / Ti));
+    const double tt = t + 1.0;
+    const double c1 = 1.0 - pow(p.beta1, tt), c2 = 1.0 - pow(p.beta2, tt);
+    sd->eta = (float)eta;
+    sd->inv_c1 = (float)(1.0 / c1);
+    sd->inv_sqrt_c2 = (float)(1.0 / sqrt(c2));
+    sd->t = t + 1;
+}
+
+__global__ void set_step_kernel(StepSched* __restrict__ sd, int t) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) sd->t = t;
+}
+
 __global__ void adam_kernel(float* __restrict__ z, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ gx, int64_t M, int npc, float eps, float eta, float b1,
-                            float b2, float inv_c1, float inv_sqrt_c2, float adam_eps) {
+                            const float* __restrict__ gx, int64_t M, int npc, float eps, float b1, float b2,
+                            float adam_eps, const StepSched* __restrict__ sd) {
+    const float eta = sd->eta, inv_c1 = sd->inv_c1, inv_sqrt_c2 = sd->inv_sqrt_c2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         float zi = z[i];
         float g = gx[i];
@@ -155,9 +186,19 @@ cudaError_t launch_ls(const float* r, const float* Fg, int64_t n, float* x, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float eta,
-                        float b1, float b2, float inv_c1, float inv_sqrt_c2, float adam_eps, cudaStream_t st) {
-    adam_kernel<<<ew_blocks(M), 256, 0, st>>>(z, m, v, gx, M, npc, eps, eta, b1, b2, inv_c1, inv_sqrt_c2, adam_eps);
+cudaError_t launch_schedule(const SchedParams& p, StepSched* sd, cudaStream_t st) {
+    schedule_kernel<<<1, 32, 0, st>>>(p, sd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(StepSched* sd, int t, cudaStream_t st) {
+    set_step_kernel<<<1, 32, 0, st>>>(sd, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float b1,
+                        float b2, float adam_eps, const StepSched* sd, cudaStream_t st) {
+    adam_kernel<<<ew_blocks(M), 256, 0, st>>>(z, m, v, gx, M, npc, eps, b1, b2, adam_eps, sd);
     return cudaGetLastError();
 }
 

@@ -197,3 +197,42 @@ def test_paper_scale_first_step_in_the_benchmark_configuration():
     assert sure.sum() > 1500
     assert np.all(np.abs(np.abs(z[sure]) - eta) < 0.05 * eta)
     np.testing.assert_allclose(z1[idx][sure], z[sure], rtol=1e-4, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["adam", "linesearch", "assa", "vcr"])
+def test_graph_replayed_steps_equal_single_steps(problem, kind):
+    """gpair_solver_steps (one step captured as a CUDA graph, replayed) gives the iterates of the
+    same number of gpair_step calls; the step counter and a checkpoint set between the two paths
+    carry over.  The launches are the same; the forward's within-bin order (atomic ranks) makes
+    two runs agree to FP32 rounding rather than bit for bit."""
+    w, G, b = problem
+    kw = dict(rule=_lib.RULE_ADAM, npc=1, eta_max=0.03, T0=5, T_mult=2.0, adam_eps=1e-20)
+    if kind == "linesearch":
+        kw = dict(rule=_lib.RULE_GD_LINESEARCH, npc=0)
+    elif kind == "assa":
+        kw.update(op=_lib.OP_ASSA, n_min=25)
+    elif kind == "vcr":
+        kw.update(vcr_lambda=1e-6, vcr_beta=0.5)
+    p = _lib.StepParams(**kw)
+    gs, arr = device_inputs(w)
+    bt = torch.as_tensor(b, device="cuda")
+    s1, s2 = _lib.Solver(gs, arr, p), _lib.Solver(gs, arr, p)
+    losses = [s1.gpair_step(bt)[0] for _ in range(7)]
+    l2, _ = s2.gpair_solver_steps(bt, 3)
+    l2b, _ = s2.gpair_solver_steps(bt, 4)
+    z1, m1, v1, t1 = s1.gpair_solver_get_state()
+    z2, m2, v2, t2 = s2.gpair_solver_get_state()
+    assert t1 == t2 == 7
+    for a, c in ((z1, z2), (m1, m2), (v1, v2)):
+        assert rel_l2(c.cpu().numpy(), a.cpu().numpy()) < 1e-5
+    assert abs(l2 - losses[2]) <= 1e-6 * losses[2] and abs(l2b - losses[6]) <= 1e-6 * losses[6]
+    # a checkpoint taken on the step path resumes on the graph path
+    s3 = _lib.Solver(gs, arr, p)
+    s3.gpair_solver_set_state(z1, m1, v1, t1)
+    s1.gpair_step(bt)
+    s3.gpair_solver_steps(bt, 1)
+    za, _, _, _ = s1.gpair_solver_get_state()
+    zb, _, _, tb = s3.gpair_solver_get_state()
+    assert tb == 8 and rel_l2(zb.cpu().numpy(), za.cpu().numpy()) < 1e-5
+    for s in (s1, s2, s3):
+        s.close()
