@@ -56,7 +56,7 @@ cudaError_t launch_ls(const float* r, const float* Fg, int64_t n, float* x, cons
 cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M, int npc, float eps, float b1,
                         float b2, float adam_eps, const StepSched* sd, cudaStream_t st);
 cudaError_t launch_schedule(const SchedParams& p, StepSched* sd, cudaStream_t st);
-cudaError_t launch_set_step(StepSched* sd, int t, cudaStream_t st);
+cudaError_t launch_set_step(StepSched* sd, int t, const SchedParams& p, cudaStream_t st);
 int red_blocks();
 bool vox_is_lattice(const GaussDev& g, const gpair_grid& og);
 cudaError_t launch_voxelize(const GaussDev& g, const gpair_grid& og, float k, float* vol, float* tmp, cudaStream_t st);
@@ -853,8 +853,9 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     cudaMemset(S->m, 0, M * 4);
     cudaMemset(S->v, 0, M * 4);
     cudaMemset(S->status, 0, sizeof(int));
-    cudaMemset(S->sd, 0, sizeof(StepSched));
     S->sched = SchedParams{prm->eta_max, prm->eta_min, prm->T_mult, prm->beta1, prm->beta2, prm->T0};
+    cudaMemset(S->sd, 0, sizeof(StepSched));
+    launch_set_step(S->sd, 0, S->sched, 0);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         gpair_solver_destroy(S);
         return GPAIR_ERR_CUDA;
@@ -1052,7 +1053,7 @@ gpair_status gpair_solver_set_state(gpair_solver* S, const float* z, const float
     if (z && cudaMemcpyAsync(S->z, z, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     if (m && cudaMemcpyAsync(S->m, m, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     if (v && cudaMemcpyAsync(S->v, v, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return GPAIR_ERR_CUDA;
-    if (launch_set_step(S->sd, t, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+    if (launch_set_step(S->sd, t, S->sched, st) != cudaSuccess) return GPAIR_ERR_CUDA;
     S->t = t;
     return GPAIR_OK;
 }

@@ -6,6 +6,8 @@
 #include "gpair_internal.cuh"
 #include "step_sched.cuh"
 
+#include <cmath>
+
 namespace gp {
 
 constexpr int RED_THREADS = 256;
@@ -81,31 +83,40 @@ __global__ void finish_kernel(const double* __restrict__ partial, int nblk, int 
 // Adam on z with gradient g_x (and the NPC chain rule g_z = g_x * 2 (z + eps)).
 // Per-step scalars of Algorithm 2 on the device, so that a step's launches do not change from one
 // step to the next (and can be replayed as a CUDA graph): the CAWR step size of step t and Adam's
-// bias corrections 1 / (1 - b1^(t+1)), 1 / sqrt(1 - b2^(t+1)).  schedule_kernel advances t.
+// bias corrections 1 / (1 - b1^(t+1)), 1 / sqrt(1 - b2^(t+1)), the powers kept as running
+// products.  One thread; FP64 only for the products (GB300's FP64 pipe is slow, and a chain of
+// FP64 pow / cos / divide took ~11 us).  schedule_kernel advances t.
 __global__ void schedule_kernel(SchedParams p, StepSched* __restrict__ sd) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int t = sd->t;
     // SGDR: periods T0, T0 T_mult, ...; T_cur counts iterations since the last restart
-    double Tcur = t, Ti = p.T0 > 0 ? p.T0 : 1;
+    const int T0 = p.T0 > 0 ? p.T0 : 1;
+    float phase;                                   // T_cur / T_i
     if (p.T_mult <= 1.0) {
-        Tcur = fmod(Tcur, Ti);
+        phase = (float)(t % T0) / (float)T0;
     } else {
+        double Tcur = t, Ti = T0;
         for (int guard = 0; Tcur >= Ti && guard < 4096; ++guard) {   // O(log t) periods
             Tcur -= Ti;
             Ti *= p.T_mult;
         }
+        phase = (float)(Tcur / Ti);
     }
-    const double eta = p.eta_min + 0.5 * (p.eta_max - p.eta_min) * (1.0 + cos(3.141592653589793 * Tcur / Ti));
-    const double tt = t + 1.0;
-    const double c1 = 1.0 - pow(p.beta1, tt), c2 = 1.0 - pow(p.beta2, tt);
-    sd->eta = (float)eta;
-    sd->inv_c1 = (float)(1.0 / c1);
-    sd->inv_sqrt_c2 = (float)(1.0 / sqrt(c2));
+    sd->eta = (float)p.eta_min + 0.5f * (float)(p.eta_max - p.eta_min) * (1.f + cospif(phase));
+    const double b1t = sd->b1t * p.beta1, b2t = sd->b2t * p.beta2;   // beta^(t+1)
+    sd->b1t = b1t;
+    sd->b2t = b2t;
+    sd->inv_c1 = 1.f / (float)(1.0 - b1t);
+    sd->inv_sqrt_c2 = rsqrtf((float)(1.0 - b2t));
     sd->t = t + 1;
 }
 
-__global__ void set_step_kernel(StepSched* __restrict__ sd, int t) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) sd->t = t;
+__global__ void set_step_kernel(StepSched* __restrict__ sd, int t, double b1t, double b2t) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sd->t = t;
+        sd->b1t = b1t;
+        sd->b2t = b2t;
+    }
 }
 
 __global__ void adam_kernel(float* __restrict__ z, float* __restrict__ m, float* __restrict__ v,
@@ -191,8 +202,9 @@ cudaError_t launch_schedule(const SchedParams& p, StepSched* sd, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_step(StepSched* sd, int t, cudaStream_t st) {
-    set_step_kernel<<<1, 32, 0, st>>>(sd, t);
+// t steps taken: the running products are beta^t.
+cudaError_t launch_set_step(StepSched* sd, int t, const SchedParams& p, cudaStream_t st) {
+    set_step_kernel<<<1, 32, 0, st>>>(sd, t, std::pow(p.beta1, (double)t), std::pow(p.beta2, (double)t));
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@ namespace gp {
 struct StepSched {
     int t;                       // steps taken
     float eta, inv_c1, inv_sqrt_c2;
+    double b1t, b2t;             // beta1^t, beta2^t (running products)
 };
 struct SchedParams {
     double eta_max, eta_min, T_mult, beta1, beta2;
