@@ -109,6 +109,9 @@ def test_size_limits_and_new_entry_points_rejected_on_the_host(lib):
     prm = _lib.StepParams(op=_lib.OP_ASSA)._c()
     assert lib.gpair_solver_create(ctypes.byref(soa), ctypes.byref(a), ctypes.byref(prm), ctypes.byref(h)) == 5
     assert not h
+    lib.gpair_solver_steps.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gpair_solver_steps(None, y, 3, None, None, None) == 1                        # no solver
     lib.gpair_pipe_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     rate = ctypes.c_double()
     assert lib.gpair_pipe_peak(2, 5, ctypes.byref(rate), None) == 1                            # unknown pipe
