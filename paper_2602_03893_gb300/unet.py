@@ -158,6 +158,21 @@ class Conv:
     relu: bool
 
 
+def layer_specs(ch=(16, 32, 64, 128)) -> dict:
+    """Every convolution of the network: name -> Conv(input channels, output channels, taps, ReLU)."""
+    c1, c2, c3, c4 = ch
+    return {
+        "e1a": Conv(CIN_PAD, c1, 27, True), "e1b": Conv(c1, c1, 27, True),
+        "e2a": Conv(c1, c2, 27, True), "e2b": Conv(c2, c2, 27, True),
+        "e3a": Conv(c2, c3, 27, True), "e3b": Conv(c3, c3, 27, True),
+        "b4a": Conv(c3, c4, 27, True), "b4b": Conv(c4, c4, 27, True),
+        "d3a": Conv(c4 + c3, c3, 27, True), "d3b": Conv(c3, c3, 27, True),
+        "d2a": Conv(c3 + c2, c2, 27, True), "d2b": Conv(c2, c2, 27, True),
+        "d1a": Conv(c2 + c1, c1, 27, True), "d1b": Conv(c1, c1, 27, True),
+        "out": Conv(c1, COUT_PAD, 1, False),
+    }
+
+
 def bf16(shape, dev):
     return torch.empty(shape, dtype=torch.bfloat16, device=dev)
 
@@ -171,17 +186,7 @@ class UNet3D:
         self.dims = tuple(int(d) for d in dims)
         assert all(d % 8 == 0 for d in self.dims), "U-Net volume sides must be divisible by 8"
         self.dev = torch.device(device)
-        c1, c2, c3, c4 = self.CH
-        self.convs = {
-            "e1a": Conv(CIN_PAD, c1, 27, True), "e1b": Conv(c1, c1, 27, True),
-            "e2a": Conv(c1, c2, 27, True), "e2b": Conv(c2, c2, 27, True),
-            "e3a": Conv(c2, c3, 27, True), "e3b": Conv(c3, c3, 27, True),
-            "b4a": Conv(c3, c4, 27, True), "b4b": Conv(c4, c4, 27, True),
-            "d3a": Conv(c4 + c3, c3, 27, True), "d3b": Conv(c3, c3, 27, True),
-            "d2a": Conv(c3 + c2, c2, 27, True), "d2b": Conv(c2, c2, 27, True),
-            "d1a": Conv(c2 + c1, c1, 27, True), "d1b": Conv(c1, c1, 27, True),
-            "out": Conv(c1, COUT_PAD, 1, False),
-        }
+        self.convs = layer_specs(self.CH)
         gen = torch.Generator(device="cpu").manual_seed(seed)
         self.w32, self.wbf, self.b32, self.bbf, self.gw, self.gb = {}, {}, {}, {}, {}, {}
         self.mw, self.vw, self.mb, self.vb = {}, {}, {}, {}

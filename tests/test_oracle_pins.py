@@ -586,3 +586,141 @@ def test_ssim_window_by_brute_force():
     sxy = ((xs - mx) * (ys - my)).sum() / (xs.size - 1)
     expect = (2 * mx * my + C1) * (2 * sxy + C2) / ((mx * mx + my * my + C1) * (sx + sy + C2))
     assert abs(metrics.ssim(xs, ys, win=win) - expect) < 1e-12
+
+
+# ---------------------------------------------------------------- U-Net reference (warm start)
+
+def _unet_weights(rng, scale=1.0):
+    from oracle import unet_ref
+
+    W, B = {}, {}
+    for n, ci, co, taps, relu in unet_ref.architecture():
+        W[n] = rng.normal(size=(co, taps, ci)) * scale * math.sqrt(2.0 / (taps * ci))
+        B[n] = rng.normal(size=co) * 0.1
+    return W, B
+
+
+def test_unet_architecture_is_the_configured_one():
+    """Four levels with 16, 32, 64 and 128 channels, one channel in and one out (the input padded
+    to 16 stored channels, the prediction channel 0 of 16 computed); two 3x3x3 convolutions per
+    level; the decoder concatenates the upsampled level with the skip.  The product network
+    (paper_2602_03893_gb300.unet) declares the same layers."""
+    from oracle import unet_ref
+    from paper_2602_03893_gb300 import unet
+
+    assert unet_ref.LEVEL_CHANNELS == (16, 32, 64, 128)
+    assert unet_ref.IN_CHANNELS == 1 and unet_ref.OUT_CHANNELS == 1
+    arch = {n: (ci, co, taps, relu) for n, ci, co, taps, relu in unet_ref.architecture()}
+    assert tuple(arch) == unet_ref.ORDER and len(arch) == 15
+    for lvl, c in enumerate(unet_ref.LEVEL_CHANNELS):
+        enc = ["e1", "e2", "e3", "b4"][lvl]
+        assert arch[enc + "a"][1] == c and arch[enc + "b"][:2] == (c, c)
+    assert arch["d3a"][0] == 128 + 64 and arch["d2a"][0] == 64 + 32 and arch["d1a"][0] == 32 + 16
+    assert arch["out"] == (16, 16, 1, False) and all(v[2] == 27 and v[3] for k, v in arch.items() if k != "out")
+    prod = unet.layer_specs(unet.UNet3D.CH)
+    assert {k: (c.cin, c.cout, c.taps, c.relu) for k, c in prod.items()} == arch
+    assert unet.CIN_PAD == unet_ref.IN_STORED and unet.COUT_PAD == unet_ref.OUT_STORED
+
+
+def test_unet_layers_against_plain_loops():
+    """3x3x3 and 1x1x1 convolutions with zero padding (with and without ReLU), 2x2x2 average
+    pooling and nearest x2 upsampling of the torch reference, against the sums written out."""
+    import torch
+
+    from oracle import unet_ref
+
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(3, 3, 4, 5))
+    for taps, relu in ((27, True), (27, False), (1, False)):
+        w = rng.normal(size=(4, taps, 3))
+        b = rng.normal(size=4)
+        ref = unet_ref.conv(torch.tensor(x)[None], torch.tensor(w), torch.tensor(b), taps, relu)[0].numpy()
+        np.testing.assert_allclose(ref, unet_ref.conv_loops(x, w, b, taps, relu), rtol=0, atol=1e-12)
+    x = rng.normal(size=(3, 4, 6, 2))
+    np.testing.assert_allclose(unet_ref.pool(torch.tensor(x)[None])[0].numpy(), unet_ref.pool_loops(x),
+                               rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(unet_ref.up(torch.tensor(x)[None])[0].numpy(), unet_ref.up_loops(x))
+    # a one-hot input places each tap where the definition says: output (z, y, x) sees tap
+    # (dz, dy, dx) from input (z + dz, y + dy, x + dx)
+    xo = np.zeros((1, 3, 3, 3))
+    xo[0, 2, 1, 0] = 1.0
+    wt = np.arange(27, dtype=float).reshape(1, 27, 1)
+    yo = unet_ref.conv(torch.tensor(xo)[None], torch.tensor(wt), torch.zeros(1, dtype=torch.float64), 27,
+                       False)[0, 0].numpy()
+    assert yo[1, 1, 1] == (1 + 1) * 9 + (0 + 1) * 3 + (-1 + 1)      # dz = 1, dy = 0, dx = -1
+
+
+def test_bf16_rounding_against_bit_pattern():
+    """torch's BF16 conversion (used by the reference's storage rounding) against round to
+    nearest even on the float32 pattern, including exact ties, subnormals and large values."""
+    import torch
+
+    from oracle import unet_ref
+
+    rng = np.random.default_rng(22)
+    base = rng.normal(size=4000).astype(np.float32) * np.float32(10.0) ** rng.integers(-30, 30, 4000).astype(np.float32)
+    # ties: a bf16 value plus exactly half of its last place, both parities of the kept bit
+    expo = rng.integers(100, 150, 2000, dtype=np.uint32) << np.uint32(23)
+    kept = rng.integers(0, 128, 2000, dtype=np.uint32) << np.uint32(16)
+    ties = (expo | kept | np.uint32(0x8000)).view(np.float32)
+    sub = (rng.integers(1, 2 ** 23, 500, dtype=np.uint32)).view(np.float32)
+    x = np.concatenate([base, ties, -ties, sub, np.float32([0.0, -0.0, 3.0e38, -3.0e38])])
+    got = torch.tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, unet_ref.bf16_round_loops(x))
+    g = torch.tensor(x.astype(np.float64), requires_grad=True)
+    (gr,) = torch.autograd.grad(unet_ref.RoundBF16.apply(g), g, torch.tensor(x.astype(np.float64)))
+    np.testing.assert_array_equal(gr.numpy(), unet_ref.bf16_round_loops(x))
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_unet_forward_against_plain_loops(bf16):
+    """The whole network (8 x 8 x 8 volume, all four levels) against the composition of the
+    written-out layers; with BF16 storage both sides round the same stored activations."""
+    import torch
+
+    from oracle import unet_ref
+
+    rng = np.random.default_rng(23)
+    W, B = _unet_weights(rng)
+    x0 = np.zeros((16, 8, 8, 8))
+    x0[0] = rng.normal(size=(8, 8, 8))
+    ref = unet_ref.unet_forward(torch.tensor(x0)[None], {k: torch.tensor(v) for k, v in W.items()},
+                                {k: torch.tensor(v) for k, v in B.items()}, bf16_storage=bf16)[0].numpy()
+    loops = unet_ref.unet_forward_loops(x0, W, B, bf16_storage=bf16)
+    assert np.abs(ref).max() > 0.1
+    err = np.linalg.norm(ref - loops) / np.linalg.norm(loops)
+    assert err <= (1e-3 if bf16 else 1e-12), err
+
+
+def test_unet_gradients_against_central_differences():
+    """torch autograd through the FP64 reference against central differences of the loop network
+    on sampled weights of five layers, a bias and an input voxel (loss = sum of c * output)."""
+    import torch
+
+    from oracle import unet_ref
+
+    rng = np.random.default_rng(24)
+    W, B = _unet_weights(rng)
+    x0 = np.zeros((16, 8, 8, 8))
+    x0[0] = rng.normal(size=(8, 8, 8))
+    cvec = rng.normal(size=(16, 8, 8, 8))
+    Wt = {k: torch.tensor(v, requires_grad=True) for k, v in W.items()}
+    Bt = {k: torch.tensor(v, requires_grad=True) for k, v in B.items()}
+    xt = torch.tensor(x0, requires_grad=True)
+    out = unet_ref.unet_forward(xt[None], Wt, Bt)[0]
+    (out * torch.tensor(cvec)).sum().backward()
+    loss = lambda W_, B_, x_: float(np.sum(cvec * unet_ref.unet_forward_loops(x_, W_, B_)))
+    probes = [("w", "e1a", (3, 13, 0)), ("w", "e3b", (5, 2, 7)), ("w", "b4a", (100, 26, 40)),
+              ("w", "d2a", (9, 4, 80)), ("w", "out", (0, 0, 11)), ("b", "d1b", (6,)), ("x", None, (0, 4, 3, 5))]
+    for kind, name, idx in probes:
+        arr = {"w": W.get(name), "b": B.get(name), "x": x0}[kind]
+        grad = {"w": Wt.get(name), "b": Bt.get(name), "x": xt}[kind].grad.numpy()[idx]
+        h = 1e-6 * max(1.0, abs(arr[idx]))
+        old = arr[idx]
+        arr[idx] = old + h
+        lp = loss(W, B, x0)
+        arr[idx] = old - h
+        lm = loss(W, B, x0)
+        arr[idx] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - grad) <= 1e-6 * max(1.0, abs(grad)), (kind, name, idx, fd, grad)

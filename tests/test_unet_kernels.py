@@ -155,17 +155,20 @@ def test_unet_forward_backward_matches_fp64_reference():
     B = {k: v.cpu().double().requires_grad_(True) for k, v in net.b32.items()}
     x0 = torch.zeros((1, unet.CIN_PAD) + dims, dtype=torch.float64)
     x0[0, 0] = x.to(torch.bfloat16).double().reshape(dims)
-    ref = unet_ref.unet_forward(x0, W, B)
-    _close(out[:, 0], ref[0, 0].reshape(-1).detach(), rel=5e-2)
+    # the reference stores every activation and every gradient reaching it in BF16, as the
+    # kernels do; its arithmetic stays FP64
+    ref = unet_ref.unet_forward(x0, W, B, bf16_storage=True)
+    _close(out[:, 0], ref[0, 0].reshape(-1).detach(), rel=1e-2)
     # gradients of the same MSE loss on channel 0
     loss = torch.mean((ref[0, 0].reshape(-1) - target.double()) ** 2)
     loss.backward()
     net.loss.zero_()
     unet.gpair_mse_loss(net.act["out"], target.cuda(), nv, unet.COUT_PAD, net.grad["out"], net.loss)
     net.backward(net.grad["out"])
-    assert abs(net.loss.item() / nv - loss.item()) <= 5e-2 * loss.item()
-    for name in ("out", "d1b", "b4a", "e1a"):
-        _close(net.gw[name].cpu(), W[name].grad, rel=0.1)
+    assert abs(net.loss.item() / nv - loss.item()) <= 1e-2 * loss.item()
+    for name in unet_ref.ORDER:
+        _close(net.gw[name].cpu(), W[name].grad, rel=1e-2)
+        _close(net.gb[name].cpu(), B[name].grad, rel=1e-2)
 
 
 def test_training_reduces_loss():
