@@ -35,7 +35,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s per IR iteration (fwd+adjoint) at 8.4M Gaussians; pair-evals/s vs FP32 peak"
 UNIT = "s/iter"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 MUFU_LANES_PER_SM = 32          # MUFU lanes per SM (ex2 measured at ~30 lane-ops / clk / SM)
@@ -286,7 +285,10 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "value": v, "unit": UNIT,
                              "sample": f"per step: forward + adjoint over all Gaussians x {ns} sensors, scaled by "
                                        f"{w.Nd}/{ns}"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            # the value is extrapolated: each step times ns sensors and scales linearly to all of them
+            "extrapolated_from_sensors": ns, "extrapolation_factor": w.Nd / ns,
+            "measured_s_per_step": v * ns / w.Nd}
     print(json.dumps(line), flush=True)
 
 
@@ -494,8 +496,9 @@ def main():
     pairs, samples = work_units(w)
     fwd_avg = fwd_ms / max(nrec, 1) / 1e3
     adj_avg = adj_ms / max(nrec, 1) / 1e3
-    p_fp32 = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    p_mufu = SM_COUNT * MUFU_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count   # queried, not assumed
+    p_fp32 = sm_count * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    p_mufu = sm_count * MUFU_LANES_PER_SM * SM_MAX_MHZ * 1e6
     names = kernel_names(w)
     kern = {}
     for op, t in (("forward", fwd_avg), ("adjoint", adj_avg)):
@@ -515,7 +518,8 @@ def main():
     roofline = {"bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": "T lane-ops/s (" + ("FP32" if kd["bound_pipe"] == "fp32" else "MUFU") + ")",
                 "frac": kd["frac"], "traffic": tr, "kernel": kd["kernel"],
-                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 / {MUFU_LANES_PER_SM} MUFU lanes x "
+                "sm_count": sm_count,
+                "peak_basis": f"{sm_count} SMs (queried) x {FP32_LANES_PER_SM} FP32 / {MUFU_LANES_PER_SM} MUFU lanes x "
                               f"{SM_MAX_MHZ:.0f} MHz (max SM clock); not in the measured-peaks file",
                 "kernels": kern}
     # both operators of the iteration together: their bounds over their measured times

@@ -363,7 +363,7 @@ cudaError_t launch_assa_forward(const GaussDev& g, const ArrDev& a, const SlabIn
     cudaError_t e = cudaFuncSetAttribute(assa_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-    assa_amax_kernel<<<4 * 152, 256, 0, st>>>(g.A, g.M, amax);
+    assa_amax_kernel<<<4 * device_sms(), 256, 0, st>>>(g.A, g.M, amax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 grid((a.Nd + ASSA_SPC - 1) / ASSA_SPC, S);
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;

@@ -67,7 +67,6 @@ using namespace gp;
 namespace {
 
 constexpr int SPC = 8;            // sensors per forward CTA (matches the kernel)
-constexpr int SM_COUNT_HINT = 152;
 
 // ---- per-(device, stream) scratch pool -------------------------------------------------
 
@@ -260,7 +259,7 @@ FwdPlan plan_forward(const GaussDev& g, const ArrDev& a) {
     FwdPlan p;
     memset(&p, 0, sizeof(p));
     const int ngroups = (a.Nd + SPC - 1) / SPC;
-    const int64_t target_S = ((int64_t)SM_COUNT_HINT * 4 * 4 + ngroups - 1) / ngroups;
+    const int64_t target_S = ((int64_t)device_sms() * 4 * 4 + ngroups - 1) / ngroups;
     if (g.grid) {
         // Compact blocks of bricks: start from 4 x 4 x 8 bricks (a cube of 32 nodes a side) and
         // halve the longest side until there are enough CTAs; the band of a block is bounded by its
@@ -975,7 +974,12 @@ gpair_status gpair_step(gpair_solver* S, const float* b, double* loss_out, doubl
         if (cudaEventRecord(ev[0], st) != cudaSuccess) return GPAIR_ERR_CUDA;
     }
     gpair_status s = step_launches(S, b, ev, st);
-    if (s != GPAIR_OK) return s;
+    if (s != GPAIR_OK) {
+        // the schedule kernel may have advanced the device step count before a later launch failed:
+        // put it back to the host count, so that a checkpoint taken now resumes with the right step
+        if (S->p.rule == GPAIR_RULE_ADAM) launch_set_step(S->sd, S->t, S->sched, st);
+        return s;
+    }
     if (ev) {
         if (cudaEventRecord(ev[5], st) != cudaSuccess) return GPAIR_ERR_CUDA;
         S->nrec += 1;
@@ -1023,7 +1027,10 @@ gpair_status gpair_solver_steps(gpair_solver* S, const float* b, int n, double* 
         S->gb = b;
     }
     for (int k = 0; k < n; ++k)
-        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) return GPAIR_ERR_CUDA;
+        if (cudaGraphLaunch(S->gexec, st) != cudaSuccess) {
+            S->t += k;      // the k replays already queued advance the device step count
+            return GPAIR_ERR_CUDA;
+        }
     S->t += n;
     return read_loss(S, st, loss_out, resid_out);
 }

@@ -296,6 +296,11 @@ struct KahanF {
     }
 };
 
+// Number of SMs of the current device (cudaDevAttrMultiProcessorCount, queried once per device and
+// cached); grid sizes and reduction partial counts are multiples of it.  Host only; returns 1 if the
+// query fails, so launches stay valid.
+int device_sms();
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicMax(status, code);
 }

@@ -11,7 +11,8 @@
 namespace gp {
 
 constexpr int MET_THREADS = 256;
-constexpr int MET_BLOCKS = 152 * 4;
+// CTAs of the persistent passes: 4 per SM of the current device.
+#define MET_BLOCKS (4 * device_sms())
 
 __global__ void zmap_kernel(const float* __restrict__ vol, int nx, int ny, int nz, float* __restrict__ out) {
     const int64_t nxy = (int64_t)nx * ny;

@@ -6,12 +6,16 @@
 #include "gpair_internal.cuh"
 #include "step_sched.cuh"
 
+#include <atomic>
 #include <cmath>
 
 namespace gp {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 4;     // block partials; a second pass sums them in order
+// Block partials of the FP64 reductions: 4 per SM of the current device; a second pass sums them in
+// order.
+int red_blocks();
+#define RED_BLOCKS red_blocks()
 
 __global__ void npc_kernel(const float* __restrict__ z, float* __restrict__ x, int64_t M, int npc, float eps) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
@@ -164,7 +168,7 @@ ls_dots_kernel(const float* __restrict__ r, const float* __restrict__ Fg, int64_
 
 static int ew_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > (int64_t)device_sms() * 32) b = (int64_t)device_sms() * 32;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -214,7 +218,30 @@ cudaError_t launch_adam(float* z, float* m, float* v, const float* gx, int64_t M
     return cudaGetLastError();
 }
 
-int red_blocks() { return RED_BLOCKS; }
+int red_blocks() { return 4 * device_sms(); }
+
+int device_sms() {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cache[MAXDEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+    if (dev < 0 || dev >= MAXDEV) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        return n;
+    }
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 
 // ---- vessel continuity regulariser (Methods: R_VCR = R_H + beta R_TV) on a lattice image --------
 // Readings of the unspecified parts: central first differences (x[i+1] - x[i-1]) / 2; second

@@ -14,6 +14,10 @@
 
 #include "../../include/gpair_unet.h"
 
+namespace gp {
+int device_sms();   // SMs of the current device (step.cu)
+}
+
 namespace {
 
 typedef uint16_t bf16_t;
@@ -365,7 +369,7 @@ __global__ void add_bf16_kernel(const bf16_t* __restrict__ a, const bf16_t* __re
 
 int blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > (int64_t)gp::device_sms() * 32) b = (int64_t)gp::device_sms() * 32;
     return (int)(b < 1 ? 1 : b);
 }
 

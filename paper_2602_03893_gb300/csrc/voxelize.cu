@@ -156,7 +156,7 @@ __global__ void vox_scatter_kernel(GaussDev g, gpair_grid og, float k, float* __
 
 static int vox_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > (int64_t)device_sms() * 32) b = (int64_t)device_sms() * 32;
     return (int)(b < 1 ? 1 : b);
 }
 
