@@ -67,15 +67,27 @@ def test_free_gaussians_per_gaussian_sigma():
         _check(w, k=k)
 
 
-def test_ragged_shapes_and_time_origin():
+@pytest.mark.parametrize("t0,nt,cut", [(6.4e-6, 437, False), (7.9e-6, 37, True)])
+def test_ragged_shapes_and_time_origin(t0, nt, cut):
     """nx not a multiple of 4 (no TMA descriptor), sensors not a multiple of 8, N_t not a
-    multiple of 4, a non-zero t0, and part of the signal outside the sample range."""
+    multiple of 4 and a non-zero t0; in the second case the record is shorter than the arrivals,
+    so every sensor's signal is cut at both ends of the record."""
     g = synth.centred_grid(13, 11, 7, 0.15e-3)
     A = np.random.default_rng(5).uniform(0.1, 1.0, g.M).astype(np.float32)
     sens = synth.cap_sensors(13, 12e-3, 170.0)
-    w = synth.Workload("ragged", g, sens, 437, A=A, t0=6.4e-6)
+    w = synth.Workload("ragged", g, sens, nt, A=A, t0=t0)
     rel, y, yo = _check(w)
-    assert np.count_nonzero(yo[:, 0]) > 0 or np.count_nonzero(yo[:, -1]) > 0 or True
+    # the same sensors over a record extended by `pad` samples on both sides (oracle only)
+    pad = 200
+    ye = oracle.forward(oracle_gaussians(w), w.sensors, w.v, w.fs, t0 - pad / w.fs, nt + 2 * pad, k=w.k)
+    np.testing.assert_allclose(ye[:, pad:pad + nt], yo, rtol=0, atol=1e-12 * np.abs(yo).max())
+    outside = np.linalg.norm(ye[:, :pad]) + np.linalg.norm(ye[:, pad + nt:])
+    if cut:
+        assert np.linalg.norm(ye[:, :pad]) > 0.1 * np.linalg.norm(yo)
+        assert np.linalg.norm(ye[:, pad + nt:]) > 0.01 * np.linalg.norm(yo)
+        assert np.count_nonzero(y[:, 0]) >= 12 and np.count_nonzero(y[:, -1]) >= 10
+    else:
+        assert outside == 0.0
 
 
 def test_edge_cases_single_gaussian_and_empty_window():

@@ -50,6 +50,43 @@ def test_adam_npc_cawr_matches_oracle(problem):
     assert rel_l2(x, xo) < 2e-3
 
 
+def test_cawr_restarts_and_resume_match_oracle(problem):
+    """The device step schedule (CAWR step size and Adam's bias corrections, from the device step
+    count) against the oracle's Algorithm 2 over 12 Adam steps with T0 = 3, T_mult = 2 and
+    eta_min > 0, so that the step size restarts at t = 3 and t = 9 inside the run.  A second solver
+    resumes from a checkpoint taken at t = 5 (set_state), continues on the graph-replay path, and
+    must land on the same iterate as the oracle at t = 12."""
+    w, G, b = problem
+    iters, eta, eta_min = 12, 0.05, 0.005
+    p = _lib.StepParams(rule=_lib.RULE_ADAM, npc=1, npc_eps=1e-8, eta_max=eta, eta_min=eta_min, T0=3,
+                        T_mult=2.0, adam_eps=1e-20)
+    x, loss, resid = _gpu_ir(w, b, iters, p)
+    xo, lo, ro = oracle.ir(G, w.sensors, w.v, w.fs, w.t0, w.Nt, b, iters, k=w.k, rule="adam", npc=True,
+                           npc_eps=1e-8, eta_max=eta, eta_min=eta_min, T0=3, Tmult=2.0, adam_eps=1e-20)
+    assert [oracle.cawr(t, eta, eta_min, 3, 2.0) for t in (0, 3, 9)] == pytest.approx([eta] * 3)
+    assert np.max(np.abs(loss - lo) / lo) < 2e-3
+    assert rel_l2(x, xo) < 2e-3
+    # checkpoint at t = 5, resumed in a fresh solver
+    gs, arr = device_inputs(w)
+    bt = torch.as_tensor(b, device="cuda")
+    s1 = _lib.Solver(gs, arr, p)
+    for _ in range(5):
+        s1.gpair_step(bt, want_loss=False)
+    z, m, v, t = s1.gpair_solver_get_state()
+    s1.close()
+    assert t == 5
+    s2 = _lib.Solver(gs, arr, p)
+    s2.gpair_solver_set_state(z, m, v, t)
+    l5, _ = s2.gpair_step(bt)                   # the loss entering iteration 6 (index 5)
+    s2.gpair_solver_steps(bt, iters - 6, want_loss=False)
+    _, _, _, t2 = s2.gpair_solver_get_state()
+    x2 = s2.gpair_solver_image().cpu().numpy()
+    s2.close()
+    assert t2 == iters
+    assert abs(l5 - lo[5]) <= 2e-3 * lo[5]
+    assert rel_l2(x2, xo) < 2e-3
+
+
 def test_line_search_matches_oracle(problem):
     w, G, b = problem
     iters = 8

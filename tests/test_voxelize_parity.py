@@ -54,3 +54,34 @@ def test_grid_gaussians_onto_other_grid():
     w = synth.tiny(1)
     og = synth.centred_grid(20, 18, 22, 0.15e-3)
     assert rel_l2(_gpu_vox(w, og, 3.0), _ora_vox(w, og, 3.0)) < 1e-4
+
+
+def test_lattice_paper_scale_sampled_crops():
+    """The benchmark's call (256 x 256 x 128 Gaussians onto their own lattice, k = 3: three
+    separable passes with 4-output runs and compile-time taps) against the oracle on 14 crops of
+    6 x 6 x 6 voxels, including faces, edges and corners of the volume.  Each crop's oracle sum
+    takes every Gaussian within k sigma of it (a lattice margin of 4 nodes at sigma = h)."""
+    w = synth.paper_scale(3)
+    g = w.grid
+    A = (np.random.default_rng(31).uniform(0.0, 1.0, g.M) ** 2).astype(np.float32)
+    ww = synth.Workload(w.name, g, w.sensors[:1], 16, A=A)
+    v = _gpu_vox(ww, g, 3.0)
+    rng = np.random.default_rng(32)
+    C, R = 6, 4
+    starts = [(0, 0, 0), (g.nx - C, g.ny - C, g.nz - C), (0, g.ny - C, 0), (g.nx - C, 0, g.nz // 2),
+              (g.nx // 2, 0, 0), (0, g.ny // 2, g.nz - C)]
+    starts += [tuple(int(rng.integers(0, n - C + 1)) for n in (g.nx, g.ny, g.nz)) for _ in range(8)]
+    A3 = A.reshape(g.nz, g.ny, g.nx)
+    for (x0, y0, z0) in starts:
+        xa, ya, za = max(0, x0 - R), max(0, y0 - R), max(0, z0 - R)
+        xb, yb, zb = min(g.nx, x0 + C + R), min(g.ny, y0 + C + R), min(g.nz, z0 + C + R)
+        # the crop's Gaussians and voxels share one lattice whose origin is 0 (voxelization depends
+        # on differences only), so that offsets of exactly k sigma stay exact ties, as on the full
+        # lattice; the crop's interior then has every Gaussian that reaches it
+        nx, ny, nz = xb - xa, yb - ya, zb - za
+        Gs = oracle.gaussians_from_grid(nx, ny, nz, 0.0, 0.0, 0.0, g.h, g.sigma,
+                                        np.ascontiguousarray(A3[za:zb, ya:yb, xa:xb]).reshape(-1))
+        full = oracle.voxelize(Gs, 3.0, nx, ny, nz, 0.0, 0.0, 0.0, g.h)
+        ref = full[z0 - za:z0 - za + C, y0 - ya:y0 - ya + C, x0 - xa:x0 - xa + C]
+        got = v[z0:z0 + C, y0:y0 + C, x0:x0 + C]
+        assert rel_l2(got, ref) < 1e-4, (x0, y0, z0, rel_l2(got, ref))

@@ -47,6 +47,30 @@ def test_paper_scale_fits_the_fixed_scratch():
     _both(w, A=x)
 
 
+def test_calls_on_a_new_stream_allocate_no_device_memory():
+    """The property the entry point exists for: once the library's kernels and its fixed array
+    are loaded on the device (the first call does that), calls on a stream the library has never
+    seen leave the device's free memory unchanged.  gpair_forward on another new stream is the
+    positive control: it grows a scratch pool for that stream, and the same measurement sees it."""
+    w = synth.tiny(1)
+    gs, arr = device_inputs(w)
+    y = torch.empty((w.Nd, w.Nt), device="cuda")
+    _lib.gpair_forward(gs, arr, y)            # loads the forward kernels
+    _lib.gpair_forward_noalloc(gs, arr, y)    # loads the fixed array and takes its address
+    s_new, s_ctrl = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        _lib.gpair_forward_noalloc(gs, arr, y, stream=s_new)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    _lib.gpair_forward(gs, arr, y, stream=s_ctrl)
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 < free1
+
+
 def test_too_large_is_rejected_without_launching():
     g = synth.centred_grid(64, 64, 64, 0.1e-3)
     free = synth.free_gaussians(g, 6)
