@@ -108,7 +108,7 @@ def kernel_names(w):
     """Kernels the library launches for the two operators on this workload: the moment kernels
     when the grid's shared sigma admits the sub-sample expansion (Delta <= sigma / 2)."""
     if w.v / w.fs <= 0.5 * w.grid.sigma:
-        return {"forward": "fwd_moment_kernel", "adjoint": "adj_moment_kernel"}
+        return {"forward": "fwd_lanes_kernel", "adjoint": "adj_moment_kernel"}
     return {"forward": "fwd_grid_kernel", "adjoint": "adj_kernel"}
 
 
@@ -512,7 +512,7 @@ def main():
                     "frac": ops / t / peak, "peak_measured": pm / 1e12, "frac_of_measured": ops / t / pm,
                     "t_bound_measured_s": max(F / (pipe_peaks["fp32"] * 1e12), X / (pipe_peaks["mufu"] * 1e12))}
     dom = "forward" if fwd_avg >= adj_avg else "adjoint"
-    src = src_hash("forward.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
+    src = src_hash("forward_lanes.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
     tr = profiled_traffic(kern[dom]["kernel"], src)
     kd = kern[dom]
     roofline = {"bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],

@@ -11,9 +11,10 @@ Two evaluations of the same definition live here:
 
 * `conv`, `pool`, `up`, `unet_forward`: torch.nn.functional on CPU in float64 (channels-first),
   differentiable with torch autograd -- what the GPU tests compare against.  With
-  `bf16_storage=True` every stored activation is rounded to BF16, and so is the gradient that
-  reaches it in the backward pass (`RoundBF16`): the storage precision the configuration fixes
-  for weights and activations, while all arithmetic stays FP64.
+  `bf16_storage=True` every stored activation (convolution outputs, pooled, upsampled and
+  concatenated tensors) is rounded to BF16, and so is the gradient that reaches it in the
+  backward pass (`RoundBF16`): the storage precision the configuration fixes for weights and
+  activations, while all arithmetic stays FP64.
 * `conv_loops`, `pool_loops`, `up_loops`, `unet_forward_loops`: the same operations written out
   as sums over taps, window cells and channels on numpy arrays, with `bf16_round_loops` as an
   independent round-to-nearest-even on the float32 bit pattern.  They pin the torch evaluation
@@ -95,9 +96,9 @@ def unet_forward(x0: torch.Tensor, W: dict, B: dict, bf16_storage: bool = False)
     e2 = c("e2b", c("e2a", s(pool(e1))))
     e3 = c("e3b", c("e3a", s(pool(e2))))
     b4 = c("b4b", c("b4a", s(pool(e3))))
-    d3 = c("d3b", c("d3a", torch.cat([s(up(b4)), e3], 1)))
-    d2 = c("d2b", c("d2a", torch.cat([s(up(d3)), e2], 1)))
-    d1 = c("d1b", c("d1a", torch.cat([s(up(d2)), e1], 1)))
+    d3 = c("d3b", c("d3a", s(torch.cat([s(up(b4)), e3], 1))))
+    d2 = c("d2b", c("d2a", s(torch.cat([s(up(d3)), e2], 1))))
+    d1 = c("d1b", c("d1a", s(torch.cat([s(up(d2)), e1], 1))))
     return c("out", d1)
 
 
@@ -175,7 +176,7 @@ def unet_forward_loops(x0: np.ndarray, W: dict, B: dict, bf16_storage: bool = Fa
     e2 = c("e2b", c("e2a", s(pool_loops(e1))))
     e3 = c("e3b", c("e3a", s(pool_loops(e2))))
     b4 = c("b4b", c("b4a", s(pool_loops(e3))))
-    d3 = c("d3b", c("d3a", np.concatenate([s(up_loops(b4)), e3], 0)))
-    d2 = c("d2b", c("d2a", np.concatenate([s(up_loops(d3)), e2], 0)))
-    d1 = c("d1b", c("d1a", np.concatenate([s(up_loops(d2)), e1], 0)))
+    d3 = c("d3b", c("d3a", s(np.concatenate([s(up_loops(b4)), e3], 0))))
+    d2 = c("d2b", c("d2a", s(np.concatenate([s(up_loops(d3)), e2], 0))))
+    d1 = c("d1b", c("d1a", s(np.concatenate([s(up_loops(d2)), e1], 0))))
     return c("out", d1)

@@ -212,7 +212,7 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
         const PairRef* refs = refs2[cur];
         if (valid) {
             float acc = 0.f;         // FP32 over the chunk's 32 sensors, Kahan across chunks
-            constexpr int UNROLL = P == 7 ? 4 : 2;   // 8 terms need the registers of the deeper unroll
+            constexpr int UNROLL = P <= 7 ? 4 : 2;   // 8 terms need the registers of the deeper unroll
 #pragma unroll UNROLL
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
@@ -226,9 +226,9 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 const float4* qp = reinterpret_cast<const float4*>(Q + ((size_t)(j0 + q) * (Nt + L) + (b + L)) * MOM_P);
                 const float4 q0 = __ldg(qp), q1 = __ldg(qp + 1);
                 float s;
-                if constexpr (P == 8) s = fmaf(q1.w, e, q1.z);
-                else s = q1.z;
-                s = fmaf(s, e, q1.y);
+                if constexpr (P == 8) s = fmaf(fmaf(q1.w, e, q1.z), e, q1.y);
+                else if constexpr (P == 7) s = fmaf(q1.z, e, q1.y);
+                else s = q1.y;
                 s = fmaf(s, e, q1.x);
                 s = fmaf(s, e, q0.w);
                 s = fmaf(s, e, q0.z);
@@ -253,12 +253,14 @@ size_t adj_moment_q_bytes(const ArrDev& a, int L) { return (size_t)a.Nd * (a.Nt 
 cudaError_t launch_adjoint_moment(const GaussDev& g, const ArrDev& a, const float* delta, float* gA,
                                   const MomentTable& T, float* Q, const cudaEvent_t* ev, cudaStream_t st) {
     dim3 qgrid((a.Nt + T.L + 255) / 256, a.Nd);
-    if (T.P == 7) adj_q_kernel<7><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
+    if (T.P == 6) adj_q_kernel<6><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
+    else if (T.P == 7) adj_q_kernel<7><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
     else adj_q_kernel<8><<<qgrid, 256, (256 + T.L) * sizeof(float), st>>>(delta, a.Nt, T, Q);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (T.P == 7) adj_moment_kernel<7><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
+    if (T.P == 6) adj_moment_kernel<6><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
+    else if (T.P == 7) adj_moment_kernel<7><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
     else adj_moment_kernel<8><<<(unsigned)g.ntiles, ADJ_THREADS, 0, st>>>(g, a, delta, Q, T, gA);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);

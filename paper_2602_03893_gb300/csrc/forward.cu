@@ -721,7 +721,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = T.L;
     const int ZS = LB + L;                 // bins of the moment band
-    static_assert(P == 7 || P == 8, "7 or 8 moments");
+    static_assert(P >= 6 && P <= 8, "6 to 8 moments");
     unsigned char* wbase = smem_raw + FWDM_HDR + (size_t)warp * fwdm_warp_bytes(TB, LB, L, P);
     float2* rec = reinterpret_cast<float2*>(wbase);
     int* off = reinterpret_cast<int*>(wbase + (size_t)TILE * 8);
@@ -927,7 +927,7 @@ fwd_moment_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, floa
                         M[3] = fmaf(wq, e3, M[3]);
                         M[4] = fmaf(wq, e4, M[4]);
                         M[5] = fmaf(wq, e5, M[5]);
-                        M[6] = fmaf(wq, e6, M[6]);
+                        if constexpr (P >= 7) M[6] = fmaf(wq, e6, M[6]);
                         if constexpr (P == 8) M[P - 1] = fmaf(wq, e4 * e3, M[P - 1]);
                     }
                     float* zp = Z + (ta + bb - zlo);
@@ -1095,7 +1095,7 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
         const int TBm = ((int)std::ceil(2.0 * brick_radius(g.h) * a.invDelta) + 8 + 3) & ~3;
         const size_t msm = FWDM_HDR + (size_t)FWD_SPC * fwdm_warp_bytes(TBm, LB, mom->L, mom->P);
         if (msm <= 227 * 1024) {
-            auto kern = mom->P == 7 ? fwd_moment_kernel<7> : fwd_moment_kernel<8>;
+            auto kern = mom->P == 6 ? fwd_moment_kernel<6> : (mom->P == 7 ? fwd_moment_kernel<7> : fwd_moment_kernel<8>);
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
             if (e != cudaSuccess) return e;
             kern<<<grid, FWD_THREADS, msm, st>>>(g, a, si, partial, rows, LB, TBm, status, tmap != nullptr,

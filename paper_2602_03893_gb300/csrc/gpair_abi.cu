@@ -23,6 +23,12 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
                            const CUtensorMap* tmap, const MomentTable* mom, cudaStream_t st);
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
+size_t fwd_lanes_smem(int NW, int NZ, int LB, int P, int L);
+int fwd_lanes_nz(float h, float invDelta);
+cudaError_t launch_slab_info_cubes(const GaussDev& g, int scx, int scy, int scz, int S, SlabInfo* si, cudaStream_t st);
+cudaError_t launch_forward_lanes(const GaussDev& g, const ArrDev& a, const SlabInfo* si, int S, float* partial,
+                                 int2* rows, int LB, int NZ, int NW, int* status, const CUtensorMap* tmap,
+                                 const MomentTable& T, cudaStream_t st);
 int adj_band_len(float rad, float smax, float k, float invDelta);
 cudaError_t launch_adjoint(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const float* delta, float* gA,
                            float* gc, float* gs, int LBA, cudaStream_t st);
@@ -176,14 +182,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 3-D map over A[nz][ny][nx] float32 with an 8 x 8 x 4 box; out-of-range elements read as 0.
-bool make_tmap(const GaussDev& g, CUtensorMap* map) {
+// 3-D map over A[nz][ny][nx] float32 with a bx x by x bz box (default: one 8 x 8 x 4 brick);
+// out-of-range elements read as 0.
+bool make_tmap(const GaussDev& g, CUtensorMap* map, int bx = BX, int by = BY, int bz = BZ) {
     if (((uintptr_t)g.A & 15) != 0 || (g.nx % 4) != 0) return false;
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4};
-    cuuint32_t box[3] = {BX, BY, BZ};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(g.A), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -208,6 +215,8 @@ struct FwdPlan {
     int TB;                // tile band entries per sensor (float, atomics)
     int PL;                // partial row length
     bool binned;           // grid mode: per-(tile, sensor) binned kernel
+    bool lanes;            // grid mode: the sensor-lane moment kernel (slabs of 8^3-node cubes)
+    int NW, NZ;            // its warps per CTA and moment-band bins
     size_t off_ti, off_si, off_rows, off_part, bytes;
 };
 
@@ -320,6 +329,103 @@ bool plan_forward_capped(const GaussDev& g, const ArrDev& a, size_t cap, FwdPlan
 
 bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T);
 
+// ---- forward plan of the sensor-lane moment kernel (grid Gaussians, shared sigma) ----------
+constexpr int CUBE_SIDE = 8;                    // lattice nodes per cube side
+constexpr size_t SMEM_PER_CTA = 227 * 1024;     // dynamic shared memory a CTA may use
+
+// Slabs are blocks of sc[0] x sc[1] x sc[2] cubes; a sensor's sample band over a block is bounded
+// by the block's diagonal plus the window.  Warps per CTA: as many (up to 4) as the shared
+// memory holds.  Returns false when one warp's bands do not fit.
+bool lanes_plan_from_blocks(FwdPlan& p, const GaussDev& g, const ArrDev& a, const MomentTable& T, const int sc[3]) {
+    const int nc[3] = {(g.nx + CUBE_SIDE - 1) / CUBE_SIDE, (g.ny + CUBE_SIDE - 1) / CUBE_SIDE,
+                       (g.nz + CUBE_SIDE - 1) / CUBE_SIDE};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    p.sbx = sc[0]; p.sby = sc[1]; p.sbz = sc[2];
+    int64_t S = 1;
+    double d2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        S *= (nc[q] + sc[q] - 1) / sc[q];
+        const double span = (std::min(sc[q] * CUBE_SIDE, nn[q]) - 1) * (double)g.h;   // centre to centre
+        d2 += span * span;
+    }
+    if (S > 65535) return false;            // slabs are the grid's y dimension
+    p.S = (int)S;
+    p.LB = ((int)std::ceil((std::sqrt(d2) + 2.0 * a.k * g.sigma) * a.invDelta) + 10 + 3) & ~3;
+    p.PL = p.LB;
+    p.NZ = fwd_lanes_nz(g.h, a.invDelta);
+    p.NW = 4;
+    while (p.NW > 0 && fwd_lanes_smem(p.NW, p.NZ, p.LB, T.P, T.L) > SMEM_PER_CTA) --p.NW;
+    if (p.NW == 0) return false;
+    p.lanes = true;
+    p.binned = true;
+    p.TB = 0;
+    plan_offsets(p, g, a);
+    return true;
+}
+
+// Start from blocks of 4 x 4 x 2 cubes (32 x 32 x 16 nodes) and halve the longest side until the
+// grid has about eight CTAs per SM (one CTA fills an SM's shared memory).
+bool plan_forward_lanes(const GaussDev& g, const ArrDev& a, const MomentTable& T, FwdPlan& out) {
+    const int nc[3] = {(g.nx + CUBE_SIDE - 1) / CUBE_SIDE, (g.ny + CUBE_SIDE - 1) / CUBE_SIDE,
+                       (g.nz + CUBE_SIDE - 1) / CUBE_SIDE};
+    int sc[3] = {std::min(4, nc[0]), std::min(4, nc[1]), std::min(2, nc[2])};
+    FwdPlan p;
+    memset(&p, 0, sizeof(p));
+    if (!lanes_plan_from_blocks(p, g, a, T, sc)) return false;
+    const int64_t target = (int64_t)device_sms() * 8;
+    for (;;) {
+        const int64_t ctas = (int64_t)p.S * ((a.Nd + 32 * p.NW - 1) / (32 * p.NW));
+        if (ctas >= target) break;
+        int best = -1;
+        for (int q = 0; q < 3; ++q)
+            if (sc[q] > 1 && (best < 0 || sc[q] > sc[best])) best = q;
+        if (best < 0) break;
+        sc[best] = (sc[best] + 1) / 2;
+        FwdPlan t;
+        memset(&t, 0, sizeof(t));
+        if (!lanes_plan_from_blocks(t, g, a, T, sc)) break;
+        p = t;
+    }
+    out = p;
+    return true;
+}
+
+// The operator's plan: the sensor-lane kernel where the expansion applies and its bands fit,
+// else the brick (grid) or tile-range (free centres) plan.
+FwdPlan plan_forward_op(const GaussDev& g, const ArrDev& a) {
+    MomentTable T;
+    FwdPlan p;
+    if (g.grid && make_moment_table(g, a, T) && plan_forward_lanes(g, a, T, p)) return p;
+    return plan_forward(g, a);
+}
+
+// The same within `cap` bytes of scratch (the allocation-free entry point): the lanes plan
+// coarsened -- its smallest block side doubled -- until its partial rows fit, else the brick or
+// tile-range plan coarsened the same way.
+bool plan_forward_op_capped(const GaussDev& g, const ArrDev& a, size_t cap, FwdPlan& out) {
+    MomentTable T;
+    FwdPlan p;
+    if (g.grid && make_moment_table(g, a, T) && plan_forward_lanes(g, a, T, p)) {
+        const int nc[3] = {(g.nx + CUBE_SIDE - 1) / CUBE_SIDE, (g.ny + CUBE_SIDE - 1) / CUBE_SIDE,
+                           (g.nz + CUBE_SIDE - 1) / CUBE_SIDE};
+        int sc[3] = {p.sbx, p.sby, p.sbz};
+        bool ok = true;
+        while (p.bytes > cap) {
+            int best = -1;
+            for (int q = 0; q < 3; ++q)
+                if (sc[q] < nc[q] && (best < 0 || sc[q] < sc[best])) best = q;
+            if (best < 0) { ok = false; break; }
+            sc[best] = std::min(nc[best], 2 * sc[best]);
+            if (!lanes_plan_from_blocks(p, g, a, T, sc)) { ok = false; break; }
+        }
+        if (ok) {
+            out = p;
+            return true;
+        }
+    }
+    return plan_forward_capped(g, a, cap, out);
+}
+
 // ev (optional): two events recorded immediately before and after the slab kernel.
 gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStream_t st, void* scratch, int* status,
                          const FwdPlan& p, const cudaEvent_t* ev = nullptr) {
@@ -330,8 +436,21 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
     float* part = reinterpret_cast<float*>(base + p.off_part);
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
-    const bool tma = g.grid && make_tmap(g, &map);   // ragged row pitch: plain brick loads instead
     cudaError_t e = cudaSuccess;
+    if (p.lanes) {
+        MomentTable mom;
+        if (!make_moment_table(g, a, mom)) return GPAIR_ERR_UNSUPPORTED;
+        const bool tma = make_tmap(g, &map, CUBE_SIDE, CUBE_SIDE, CUBE_SIDE);   // ragged pitch: plain loads
+        e = launch_slab_info_cubes(g, p.sbx, p.sby, p.sbz, p.S, si, st);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess)
+            e = launch_forward_lanes(g, a, si, p.S, part, rows, p.LB, p.NZ, p.NW, status, tma ? &map : nullptr, mom,
+                                     st);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_slab_reduce(g, a, part, rows, p.S, p.PL, y, st);
+        return cuda_status(e);
+    }
+    const bool tma = g.grid && make_tmap(g, &map);   // ragged row pitch: plain brick loads instead
     if (g.grid) {
         e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
     } else {
@@ -350,11 +469,15 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
 }
 
 // Coefficients of the sub-sample expansion (MomentTable, gpair_internal.cuh) for a shared sigma.
-// K(d) = d exp(-d^2/2s^2) has derivatives K^(p)(d) = s^(1-p) (-1)^p He_{p+1}(u) exp(-u^2/2),
-// u = d / s, with He the probabilists' Hermite polynomials.  Returns false when the expansion
-// does not apply (window longer than MOM_LMAX samples, or Delta > sigma / 2 where 8 terms no
-// longer reach 1e-6).  The number of terms kept (7 or 8) is the smallest whose truncation error,
-// evaluated against the pulse on 129 offsets per position, is below 3e-7 of its peak.
+// For window position m the pulse, as a function of the offset e in [-1, 1],
+//     K_m(e) = (1/2) d exp(-d^2 / 2 s^2),  d = dstar - m Delta + e Delta / 2
+// (with the 1/2 of A / 2R), is replaced by the polynomial of degree P - 1 that interpolates it at
+// the 64 Chebyshev points e_i = cos(pi (i + 1/2) / 64), truncated to its first P Chebyshev terms
+// (the discrete least-squares fit in the Chebyshev basis, close to the best uniform fit), and
+// written in monomials: K_m(e) ~ sum_p c[m][p] e^p.  P is the smallest of 6, 7, 8 whose
+// largest error, evaluated against the pulse at 257 offsets per position, is below 3e-7 of the
+// pulse's peak.  Returns false when the expansion does not apply (window longer than MOM_LMAX
+// samples, or Delta > sigma / 2).
 bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
     if (!g.grid) return false;
     const double s = g.sigma, Delta = (double)a.Delta, k = a.k;
@@ -374,36 +497,48 @@ bool make_moment_table(const GaussDev& g, const ArrDev& a, MomentTable& T) {
     T.e_thr = (float)(((double)E * Delta - k * s - dstar) * (2.0 / Delta));
     for (int m = 0; m < MOM_LMAX; ++m)
         for (int p = 0; p < MOM_P; ++p) T.c[m][p] = 0.f;
-    static thread_local double cd[MOM_LMAX][MOM_P];
-    for (int m = 0; m < L; ++m) {
-        const double u = (dstar - m * Delta) / s;
-        double He[MOM_P + 2];
-        He[0] = 1.0;
-        He[1] = u;
-        for (int n = 1; n <= MOM_P; ++n) He[n + 1] = u * He[n] - n * He[n - 1];
-        const double eu = std::exp(-0.5 * u * u);
-        double fact = 1.0, hp = 1.0, sp = s;   // p!, (Delta/2)^p, s^(1-p)
-        for (int p = 0; p < MOM_P; ++p) {
-            if (p > 0) { fact *= p; hp *= 0.5 * Delta; sp /= s; }
-            const double deriv = sp * ((p & 1) ? -1.0 : 1.0) * He[p + 1] * eu;
-            cd[m][p] = 0.5 * deriv * hp / fact;     // with the 1/2 of A / 2R
-        }
-    }
-    // truncation error of the first P terms against the pulse itself
+    auto pulse = [&](int m, double e) {
+        const double d = dstar - m * Delta + 0.5 * Delta * e;
+        return 0.5 * d * std::exp(-0.5 * d * d / (s * s));
+    };
+    constexpr int NC = 64;                       // Chebyshev points
+    // monomial coefficients of the Chebyshev polynomials T_0 .. T_{MOM_P-1}
+    double Tm[MOM_P][MOM_P] = {};
+    Tm[0][0] = 1.0;
+    Tm[1][1] = 1.0;
+    for (int n = 2; n < MOM_P; ++n)
+        for (int q = 0; q < MOM_P; ++q) Tm[n][q] = (q > 0 ? 2.0 * Tm[n - 1][q - 1] : 0.0) - Tm[n - 2][q];
     const double peak = 0.5 * s * std::exp(-0.5);
-    double err7 = 0.0;
-    for (int m = 0; m < L; ++m)
-        for (int q = 0; q <= 128; ++q) {
-            const double e = -1.0 + q / 64.0;
-            const double d = dstar - m * Delta + 0.5 * Delta * e;
-            const double K = 0.5 * d * std::exp(-0.5 * d * d / (s * s));
-            double ser = 0.0, ep = 1.0;
-            for (int p = 0; p < 7; ++p, ep *= e) ser += cd[m][p] * ep;
-            err7 = std::max(err7, std::fabs(K - ser) / peak);
+    static thread_local double cd[MOM_LMAX][MOM_P];
+    int P = MOM_P;
+    for (int PP = 6; PP <= MOM_P; ++PP) {
+        double err = 0.0;
+        for (int m = 0; m < L; ++m) {
+            double ch[MOM_P] = {};             // Chebyshev coefficients from the discrete orthogonality
+            for (int i = 0; i < NC; ++i) {
+                const double th = M_PI * (i + 0.5) / NC;
+                const double f = pulse(m, std::cos(th));
+                for (int n = 0; n < PP; ++n) ch[n] += f * std::cos(n * th);
+            }
+            for (int n = 0; n < PP; ++n) ch[n] *= (n == 0 ? 1.0 : 2.0) / NC;
+            for (int q = 0; q < MOM_P; ++q) {
+                double c = 0.0;
+                for (int n = 0; n < PP; ++n) c += ch[n] * Tm[n][q];
+                cd[m][q] = q < PP ? c : 0.0;
+            }
+            for (int q = 0; q <= 256; ++q) {
+                const double e = -1.0 + q / 128.0;
+                double ser = 0.0, ep = 1.0;
+                for (int p = 0; p < PP; ++p, ep *= e) ser += cd[m][p] * ep;
+                err = std::max(err, std::fabs(pulse(m, e) - ser) / peak);
+            }
         }
-    T.P = err7 <= 3e-7 ? 7 : MOM_P;
+        P = PP;
+        if (err <= 3e-7) break;
+    }
+    T.P = P;
     for (int m = 0; m < L; ++m)
-        for (int p = 0; p < T.P; ++p) T.c[m][p] = (float)cd[m][p];
+        for (int p = 0; p < P; ++p) T.c[m][p] = (float)cd[m][p];
     return true;
 }
 
@@ -450,7 +585,7 @@ gpair_status forward_into_scratch(const gpair_gaussians* gi, const gpair_array* 
     if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
     if (!y) return GPAIR_ERR_INVALID_ARG;
     FwdPlan p;
-    if (!plan_forward_capped(g, a, cap, p)) return GPAIR_ERR_TOO_LARGE;
+    if (!plan_forward_op_capped(g, a, cap, p)) return GPAIR_ERR_TOO_LARGE;
     return run_forward(g, a, y, st, scratch, status, p);
 }
 }  // namespace gp
@@ -484,7 +619,7 @@ gpair_status gpair_forward(const gpair_gaussians* gi, const gpair_array* ai, flo
     if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
     if (!y) return GPAIR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    FwdPlan p = plan_forward(g, a);
+    FwdPlan p = plan_forward_op(g, a);
     void* scratch = nullptr;
     int* status = nullptr;
     if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
@@ -830,7 +965,7 @@ gpair_status gpair_solver_create(const gpair_gaussians* gi, const gpair_array* a
     }
     const size_t M = (size_t)g.M, N = (size_t)a.Nd * a.Nt;
     if (assa) S->aa = assa_band_array(g, a, S->T);
-    S->plan = plan_forward(g, assa ? S->aa : a);
+    S->plan = assa ? plan_forward(g, S->aa) : plan_forward_op(g, a);
     const size_t qbytes = assa ? 0 : adjoint_q_bytes(g, a);
     bool ok = cudaMalloc(&S->z, M * 4) == cudaSuccess && cudaMalloc(&S->m, M * 4) == cudaSuccess &&
               cudaMalloc(&S->v, M * 4) == cudaSuccess && cudaMalloc(&S->x, M * 4) == cudaSuccess &&

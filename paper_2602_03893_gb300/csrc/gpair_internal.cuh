@@ -87,21 +87,22 @@ struct PairRef {
 // Sub-sample expansion of the windowed pulse for a shared sigma.  A pair's window starts at the
 // first sample whose phase d0 satisfies d0 <= k sigma, so d0 lies in (k sigma - Delta, k sigma].
 // Writing d0 = dstar + e * Delta / 2 with dstar = k sigma - Delta / 2 and e in (-1, 1], the
-// pulse K(d) = d exp(-d^2 / 2 sigma^2) at window position m is the Taylor series
-//     K(d0 - m Delta) = sum_p c[m][p] e^p,  c[m][p] = K^(p)(dstar - m Delta) (Delta/2)^p / p!,
-// truncated after MOM_P terms (relative error < 1e-7 for Delta <= 0.75 sigma).  Positions
+// pulse K(d) = d exp(-d^2 / 2 sigma^2) at window position m is a smooth function of e, replaced
+// by a polynomial of degree P - 1,
+//     K(d0 - m Delta) ~ sum_p c[m][p] e^p,
+// the Chebyshev-point fit of the host (make_moment_table), whose largest error over every
+// position and offset stays below 3e-7 of the pulse's peak (P = 6 at Delta = 0.375 sigma, the
+// 0.1 mm / 40 MHz workloads; 7 or 8 up to Delta = sigma / 2).  Positions
 // m < E = floor(2 k sigma / Delta) are always inside the window, position E is inside when
 // d0 - E Delta >= -k sigma (for a fraction 2 k sigma / Delta - E of the pairs), later positions
 // never.  The table covers positions m < L: L = E + 1 when position E is inside for most pairs
 // (edge_in = 1; the pairs for which it is outside subtract its term, evaluated directly), else
 // L = E (the pairs for which it is inside add its term).  The coefficients carry the factor 1/2 of
-// the weight A / 2R, so that a pair's weight is A / R.  The host keeps the first P = 7 terms when
-// their truncation error, evaluated over every position and offset, stays below 3e-7 of the
-// pulse's peak, and all MOM_P = 8 otherwise.
+// the weight A / 2R, so that a pair's weight is A / R.
 constexpr int MOM_P = 8;
 constexpr int MOM_LMAX = 128;
 struct MomentTable {
-    int P;                       // terms used (7 or 8; c[m][p] = 0 for p >= P)
+    int P;                       // terms used (6, 7 or 8; c[m][p] = 0 for p >= P)
     int L;                       // positions covered by the expansion
     int E;                       // edge position
     int edge_in;                 // 1: the table covers position E

@@ -144,6 +144,13 @@ def test_pool_up_concat_relu():
 
 
 def test_unet_forward_backward_matches_fp64_reference():
+    """The whole network against the FP64 reference that stores activations and gradients in BF16
+    as the kernels do.  Layer by layer (each convolution's weight and data gradient recomputed in
+    FP64 from the kernels' own stored BF16 input and masked output gradient) the kernels agree to
+    FP32 accumulation (weight gradients, 1e-5) and to the BF16 rounding of their output (data
+    gradients, 3e-3).  Through the whole 15-layer network those independent BF16 roundings
+    compound: the output agrees to 1e-2 and every layer's weight and bias gradient to 8e-2 (measured:
+    3e-3 on the output; 2e-4 to 5.3e-2 on the weight gradients, largest at the bottleneck)."""
     dims = (8, 16, 16)
     net = unet.UNet3D(dims, seed=1)
     gen = torch.Generator().manual_seed(5)
@@ -155,8 +162,6 @@ def test_unet_forward_backward_matches_fp64_reference():
     B = {k: v.cpu().double().requires_grad_(True) for k, v in net.b32.items()}
     x0 = torch.zeros((1, unet.CIN_PAD) + dims, dtype=torch.float64)
     x0[0, 0] = x.to(torch.bfloat16).double().reshape(dims)
-    # the reference stores every activation and every gradient reaching it in BF16, as the
-    # kernels do; its arithmetic stays FP64
     ref = unet_ref.unet_forward(x0, W, B, bf16_storage=True)
     _close(out[:, 0], ref[0, 0].reshape(-1).detach(), rel=1e-2)
     # gradients of the same MSE loss on channel 0
@@ -167,8 +172,26 @@ def test_unet_forward_backward_matches_fp64_reference():
     net.backward(net.grad["out"])
     assert abs(net.loss.item() / nv - loss.item()) <= 1e-2 * loss.item()
     for name in unet_ref.ORDER:
-        _close(net.gw[name].cpu(), W[name].grad, rel=1e-2)
-        _close(net.gb[name].cpu(), B[name].grad, rel=1e-2)
+        _close(net.gw[name].cpu(), W[name].grad, rel=8e-2)
+        _close(net.gb[name].cpu(), B[name].grad, rel=8e-2)
+    # layer by layer on the kernels' own stored tensors (relu_bwd has masked net.grad in place)
+    lv = [(dims[0] >> q, dims[1] >> q, dims[2] >> q) for q in range(4)]
+    inputs = {"e1a": ("x", 0), "e1b": ("e1a", 0), "e2a": ("p1", 1), "e2b": ("e2a", 1), "e3a": ("p2", 2),
+              "e3b": ("e3a", 2), "b4a": ("p3", 3), "b4b": ("b4a", 3), "d3a": ("k3", 2), "d3b": ("d3a", 2),
+              "d2a": ("k2", 1), "d2b": ("d2a", 1), "d1a": ("k1", 0), "d1b": ("d1a", 0), "out": ("d1b", 0)}
+    assert set(inputs) == set(unet_ref.ORDER)
+    for name, (src, l) in inputs.items():
+        c = net.convs[name]
+        xin = _cl_to_cf(net.act[src].cpu(), lv[l]).requires_grad_(True)
+        wr = net.wbf[name].cpu().double().requires_grad_(True)
+        y = unet_ref.conv(xin, wr, net.b32[name].cpu().double(), c.taps, False)
+        y.backward(_cl_to_cf(net.grad[name].cpu(), lv[l]))
+        _close(net.gw[name].cpu(), wr.grad, rel=1e-5)
+        if name != "e1a":
+            gin = xin.grad
+            if src in net.convs and net.convs[src].relu:
+                gin = gin * (_cl_to_cf(net.act[src].cpu(), lv[l]) > 0)
+            _close(_cl_to_cf(net.grad[src].cpu(), lv[l]), gin, rel=3e-3)
 
 
 def test_training_reduces_loss():

@@ -50,9 +50,11 @@ def test_paper_scale_fits_the_fixed_scratch():
 def test_calls_on_a_new_stream_allocate_no_device_memory():
     """The property the entry point exists for: once the library's kernels and its fixed array
     are loaded on the device (the first call does that), calls on a stream the library has never
-    seen leave the device's free memory unchanged.  gpair_forward on another new stream is the
-    positive control: it grows a scratch pool for that stream, and the same measurement sees it."""
-    w = synth.tiny(1)
+    seen leave the device's free memory unchanged.  The problem (1.05 M Gaussians, 1024 x 4096
+    samples) needs tens of MB of scratch, so an allocation would show; gpair_forward on another
+    new stream is the positive control: it grows a scratch pool for that stream, and the same
+    measurement sees it."""
+    w = synth.mid(2)
     gs, arr = device_inputs(w)
     y = torch.empty((w.Nd, w.Nt), device="cuda")
     _lib.gpair_forward(gs, arr, y)            # loads the forward kernels
@@ -68,7 +70,7 @@ def test_calls_on_a_new_stream_allocate_no_device_memory():
     _lib.gpair_forward(gs, arr, y, stream=s_ctrl)
     torch.cuda.synchronize()
     free2, _ = torch.cuda.mem_get_info()
-    assert free2 < free1
+    assert free1 - free2 >= 8 << 20
 
 
 def test_too_large_is_rejected_without_launching():
