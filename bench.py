@@ -63,7 +63,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sensors", type=int, default=32)
     p.add_argument("--no-assa", action="store_true",
-                   help="skip timing the paper's ASSA operator, the regulariser, voxelization and the image metrics")
+                   help="skip timing the paper's ASSA operator, the regulariser, voxelization, the image metrics "
+                        "and the differentiation workload")
+    p.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start comparison (~3 min)")
+    p.add_argument("--ws-train", type=int, default=2000)
+    p.add_argument("--ws-eval", type=int, default=200)
+    p.add_argument("--ws-epochs", type=int, default=1)
     return p.parse_args()
 
 
@@ -95,6 +100,12 @@ FP32_PER_SAMPLE = {"forward": 4.0, "adjoint": 5.0}
 FP32_PER_PAIR = 10.0
 MUFU_PER_SAMPLE = 1.0
 MUFU_PER_PAIR = 2.0
+# The full gradient (amplitude, centre, width) of the direct windowed evaluation: per sample-eval
+# the phase, the exponential and four accumulated moments of delta e (delta e d^0..3): 10 FP32
+# ops and 1 MUFU; per pair the phase and weight (10 FP32, 2 MUFU) plus the gradient assembly
+# (dp/dR, the three centre components, dp/dsigma, and their sums over sensors: 30 FP32, 2 MUFU).
+FULL_FP32_PER_SAMPLE, FULL_FP32_PER_PAIR = 10.0, 40.0
+FULL_MUFU_PER_SAMPLE, FULL_MUFU_PER_PAIR = 1.0, 4.0
 
 
 def alg_work(w, op):
@@ -110,6 +121,94 @@ def kernel_names(w):
     if w.v / w.fs <= 0.5 * w.grid.sigma:
         return {"forward": "fwd_lanes_kernel", "adjoint": "adj_moment_kernel"}
     return {"forward": "fwd_grid_kernel", "adjoint": "adj_kernel"}
+
+
+def diff_leg(args, dev, stream, p_fp32, p_mufu, pipe_peaks, world):
+    """The differentiation workload: 262,144 free Gaussians (64^3 lattice jittered by U[+-0.05] mm,
+    sigma log-uniform 0.05-0.2 mm), 512 sensors x 2048 samples.  Amplitudes dense (U[0,1]^2, as
+    an optimisation iterate has them).  Times gpair_forward (free centres: tile and slab summaries,
+    fwd_slab_kernel, slab reduction) and gpair_adjoint with all three gradients (tile summaries,
+    adj_kernel with the centre and width derivatives) on the stream, CUDA events, after warm-up."""
+    import torch
+
+    from paper_2602_03893_gb300 import _lib, synth
+    w = synth.differentiable(4)
+    cx, cy, cz, sg, _ = w.free
+    rng = np.random.default_rng(9)
+    A = (rng.uniform(0.0, 1.0, w.M) ** 2).astype(np.float32)
+    t = lambda q: torch.as_tensor(np.ascontiguousarray(q, dtype=np.float32), device=dev)
+    gs = _lib.Gaussians(A=t(A), cx=t(cx), cy=t(cy), cz=t(cz), sigma=t(sg))
+    arr = _lib.SensorArray(xyz=t(w.sensors), sound_speed=w.v, fs=w.fs, n_samples=w.Nt, t0=w.t0, window_k=w.k)
+    y = torch.empty((w.Nd, w.Nt), device=dev)
+    d = torch.randn((w.Nd, w.Nt), device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+    gA, gc, gsg = torch.empty(w.M, device=dev), torch.empty((3, w.M), device=dev), torch.empty(w.M, device=dev)
+    fns = {"forward": lambda: _lib.gpair_forward(gs, arr, y),
+           "adjoint_full": lambda: _lib.gpair_adjoint(gs, arr, d, gA, gc, gsg)}
+    times = {}
+    reps = max(3, min(args.steps, 10))
+    for name, fn in fns.items():
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = max_over_ranks(a0.elapsed_time(a1) / reps, world) / 1e3
+    assert _lib.gpair_last_device_status() == 0
+    pairs = float(w.M) * w.Nd
+    mean_sigma = float(np.mean(sg.astype(np.float64)))
+    samples = pairs * 2.0 * w.k * mean_sigma * w.fs / w.v
+    work = {"forward": (FP32_PER_SAMPLE["forward"] * samples + FP32_PER_PAIR * pairs,
+                        MUFU_PER_SAMPLE * samples + MUFU_PER_PAIR * pairs),
+            "adjoint_full": (FULL_FP32_PER_SAMPLE * samples + FULL_FP32_PER_PAIR * pairs,
+                             FULL_MUFU_PER_SAMPLE * samples + FULL_MUFU_PER_PAIR * pairs)}
+    out = {"workload": w.name, "gaussians": w.M, "sensors": w.Nd, "samples": w.Nt, "pairs": pairs,
+           "sample_evals": samples, "amplitudes": "dense U[0,1]^2", "reps": reps,
+           "kernels": {"forward": "fwd_slab_kernel", "adjoint_full": "adj_kernel (A, c, sigma)"}}
+    for name, (F, X) in work.items():
+        tm = times[name]
+        t_fp32, t_mufu = F / p_fp32, X / p_mufu
+        pipe = "fp32" if t_fp32 >= t_mufu else "mufu"
+        ops, peak = (F, p_fp32) if pipe == "fp32" else (X, p_mufu)
+        pm = pipe_peaks[pipe] * 1e12
+        out[name] = {"ms": tm * 1e3, "alg_fp32_ops": F, "alg_mufu_ops": X, "bound_pipe": pipe,
+                     "achieved": ops / tm / 1e12, "peak": peak / 1e12, "frac": ops / tm / peak,
+                     "frac_of_measured": ops / tm / pm, "pair_evals_per_s": pairs / tm,
+                     "includes": ("tile and slab summaries + fwd_slab_kernel + slab reduction" if name == "forward"
+                                  else "tile summaries + adj_kernel with centre and width gradients")}
+    return out
+
+
+def warmstart_leg(args):
+    """The learned warm start at the mid geometry (128 x 128 x 64 Gaussians, 1024 sensors x 4096
+    samples): the BF16 U-Net trained on `ws_train` seeded vessel-tree phantoms whose signals come
+    from gpair_forward (the library's kernels do the data, the training and the reconstructions),
+    then on `ws_eval` held-out seeds the plain reconstruction (Algorithm 2 from zero, the
+    configuration's 50 iterations, its best step size) against A^T b -> network -> the same solver
+    until the plain final residual is reached within a relative 1e-3.  Device seconds per
+    reconstruction; the one-time training is reported separately (not in warm_s) with the number of
+    reconstructions that pays it back."""
+    from paper_2602_03893_gb300 import warmstart
+    procs = max(1, min(16, len(os.sched_getaffinity(0))))
+    t0 = time.perf_counter()
+    rep, _ = warmstart.run(n_train=args.ws_train, n_eval=args.ws_eval, n_timed=args.ws_eval, epochs=args.ws_epochs,
+                           lr=1e-3, iters=50, procs=procs, log=None)
+    wall = time.perf_counter() - t0
+    rows = rep["rows"]
+    gain = rep["plain_s_mean"] - rep["warm_s_mean"]
+    return {"workload": rep["workload"], "n_train": rep["n_train"], "epochs": rep["epochs"], "n_seeds": len(rows),
+            "reached_frac": rep["reached_frac"], "plain_s": rep["plain_s_mean"], "warm_s": rep["warm_s_mean"],
+            "plain_iters": rep["ir_iters"], "warm_iters_mean": rep["warm_iters_mean"],
+            "warm_iters_max": max(r["warm_iters"] for r in rows), "eta_plain": rep["eta"], "eta_warm": rep["eta_warm"],
+            "warm_net_s_mean": float(np.mean([r["warm_net_s"] for r in rows])),
+            "x0_rel_err_mean": rep["x0_rel_err_mean"], "train_s": rep["train_s"], "data_s": rep["data_s"],
+            "train_loss_first": rep["train_loss_first"], "train_loss_last": rep["train_loss_last"],
+            "training_included_in_warm_s": False,
+            "break_even_reconstructions": (rep["train_s"] / gain) if gain > 0 else None,
+            "target": "warm residual <= (1 + 1e-3) x plain residual after 50 iterations", "leg_wall_s": wall}
 
 
 def src_hash(*names):
@@ -531,6 +630,13 @@ def main():
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = kd["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
 
+    diff = None
+    if not args.no_assa:
+        diff = diff_leg(args, dev, stream, p_fp32, p_mufu, pipe_peaks, world)
+    ws = None
+    if not args.no_warmstart and rank == 0 and world == 1:
+        ws = warmstart_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, min(args.cpu_sensors, w.Nd))
@@ -548,7 +654,7 @@ def main():
                 "kernel_ms": {"forward": fwd_avg * 1e3, "adjoint": adj_avg * 1e3,
                               "step_device": step_ms / max(nrec, 1)},
                 "graph_ms_per_step": graph_ms,
-                "roofline": roofline, "assa": assa, "vcr": vcr, "voxelize": vox, "metrics": met,
+                "roofline": roofline, "assa": assa, "vcr": vcr, "voxelize": vox, "metrics": met, "diff": diff, "warmstart": ws,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
