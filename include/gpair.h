@@ -131,6 +131,34 @@ gpair_status gpair_adjoint(const gpair_gaussians* g, const gpair_array* arr, con
                            float* gA, float* gc, float* gsigma, void* stream);
 
 /* ----------------------------------------------------------------------------------------
+ * The operator partitioned over Gaussians (z-slabs of a grid-implicit set), for running it on
+ * several GPUs.  Eq. single_forward is a sum over Gaussians, so the signals split into
+ * per-slab partial signals that add up to y (one all-reduce per forward), and the adjoint of
+ * each Gaussian depends only on the residual, so each slab's amplitude gradient is computed
+ * without communication.  Shard s of n owns the lattice rows iz in [z_begin, z_end): the rows
+ * are dealt out in order, the first nz % n shards taking one row more.
+ *
+ * gpair_shard_range: that row range (host arithmetic only; no device is touched).
+ * INVALID_ARG for a NULL pointer, n_shards < 1 or shard outside [0, n_shards); a shard may own
+ * no rows (z_begin == z_end) when n_shards > nz. */
+gpair_status gpair_shard_range(const gpair_grid* grid, int shard, int n_shards, int* z_begin, int* z_end);
+
+/* gpair_forward_shard: the forward operator of the shard's Gaussians only,
+ *     y_s[j][n] = sum over i with iz(i) in [z_begin, z_end) of the terms of gpair_forward,
+ * so that sum_s y_s = y.  g must be grid-implicit and describe the WHOLE lattice (A: device
+ * [M], of which only the shard's rows are read).  y: device [n_sensors][n_samples], overwritten
+ * (zeros when the shard owns no rows).  Same accuracy as gpair_forward; UNSUPPORTED for a
+ * free-centre set. */
+gpair_status gpair_forward_shard(const gpair_gaussians* g, const gpair_array* arr, int shard, int n_shards,
+                                 float* y, void* stream);
+
+/* gpair_adjoint_shard: the amplitude gradient (gpair_adjoint's gA) of the shard's Gaussians:
+ * gA[i] for iz(i) in [z_begin, z_end) is overwritten, every other entry is left untouched.
+ * gA: device [M].  delta: device [n_sensors][n_samples], the full residual. */
+gpair_status gpair_adjoint_shard(const gpair_gaussians* g, const gpair_array* arr, int shard, int n_shards,
+                                 const float* delta, float* gA, void* stream);
+
+/* ----------------------------------------------------------------------------------------
  * gpair_voxelize -- Eq. (2) sampled on a voxel grid (Methods, the continuous source field):
  *     V[v] = sum_i A_i prod_a [|r_a - c_a| <= k sigma_i] exp(-(r_a - c_a)^2 / 2 sigma_i^2)
  * at voxel centres of out_grid (host pointer; its sigma field is ignored), box-truncated at

@@ -24,7 +24,8 @@ RULE_ADAM, RULE_GD_LINESEARCH = 0, 1
 OP_EXACT, OP_ASSA = 0, 1          # gpair_step_params.op
 
 # Symbols declared in include/gpair.h (checked by the CPU test suite).
-EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
+EXPORTS = ("gpair_forward", "gpair_forward_noalloc", "gpair_adjoint", "gpair_shard_range", "gpair_forward_shard",
+           "gpair_adjoint_shard", "gpair_voxelize", "gpair_solver_create", "gpair_solver_destroy",
            "gpair_step", "gpair_solver_image", "gpair_solver_get_state", "gpair_solver_set_state",
            "gpair_solver_profile", "gpair_solver_timings", "gpair_solver_steps",
            "gpair_reduce_f64", "gpair_status_string", "gpair_last_device_status", "gpair_release_scratch",
@@ -72,6 +73,10 @@ def load(path: str | None = None):
         lib.gpair_forward.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P]
         lib.gpair_forward_noalloc.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P]
         lib.gpair_adjoint.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), P, P, P, P, P]
+        lib.gpair_shard_range.argtypes = [ctypes.POINTER(_Grid), c_int, c_int, ctypes.POINTER(c_int),
+                                          ctypes.POINTER(c_int)]
+        lib.gpair_forward_shard.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), c_int, c_int, P, P]
+        lib.gpair_adjoint_shard.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array), c_int, c_int, P, P, P]
         lib.gpair_voxelize.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Grid), c_float, P, P]
         lib.gpair_solver_create.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Array),
                                             ctypes.POINTER(_StepParams), ctypes.POINTER(c_void_p)]
@@ -228,6 +233,37 @@ def gpair_adjoint(g: Gaussians, arr: SensorArray, delta: torch.Tensor, gA: torch
     _check("gpair_adjoint", lib.gpair_adjoint(ctypes.byref(gc_), ctypes.byref(ac), _ptr(delta), _ptr(gA), _ptr(gc),
                                               _ptr(gsigma), _stream(stream)))
     return gA, gc, gsigma
+
+
+def gpair_shard_range(grid: Grid, shard: int, n_shards: int):
+    """Lattice rows [z_begin, z_end) of shard `shard` of `n_shards` (host arithmetic)."""
+    zb, ze = c_int(0), c_int(0)
+    gr = grid._c()
+    _check("gpair_shard_range", load().gpair_shard_range(ctypes.byref(gr), int(shard), int(n_shards), ctypes.byref(zb),
+                                                         ctypes.byref(ze)))
+    return zb.value, ze.value
+
+
+def gpair_forward_shard(g: Gaussians, arr: SensorArray, shard: int, n_shards: int, y: torch.Tensor,
+                        stream=None) -> torch.Tensor:
+    """Partial signals of the shard's z-slab of a grid-implicit set (they sum to gpair_forward)."""
+    lib = load()
+    gc_, keep = g._c()
+    ac = arr._c()
+    _check("gpair_forward_shard", lib.gpair_forward_shard(ctypes.byref(gc_), ctypes.byref(ac), int(shard),
+                                                          int(n_shards), _ptr(y), _stream(stream)))
+    return y
+
+
+def gpair_adjoint_shard(g: Gaussians, arr: SensorArray, shard: int, n_shards: int, delta: torch.Tensor,
+                        gA: torch.Tensor, stream=None) -> torch.Tensor:
+    """Amplitude gradient of the shard's Gaussians (its rows of gA; the rest untouched)."""
+    lib = load()
+    gc_, keep = g._c()
+    ac = arr._c()
+    _check("gpair_adjoint_shard", lib.gpair_adjoint_shard(ctypes.byref(gc_), ctypes.byref(ac), int(shard),
+                                                          int(n_shards), _ptr(delta), _ptr(gA), _stream(stream)))
+    return gA
 
 
 def gpair_assa_forward(g: Gaussians, arr: SensorArray, y: torch.Tensor, n_min: int = 25, stream=None) -> torch.Tensor:

@@ -643,6 +643,82 @@ gpair_status gpair_adjoint(const gpair_gaussians* gi, const gpair_array* ai, con
                        q_bytes ? static_cast<char*>(scratch) + ti_bytes : nullptr);
 }
 
+gpair_status gpair_shard_range(const gpair_grid* grid, int shard, int n_shards, int* z_begin, int* z_end) {
+    if (!grid || !z_begin || !z_end || n_shards < 1 || shard < 0 || shard >= n_shards || grid->nz < 0)
+        return GPAIR_ERR_INVALID_ARG;
+    const int64_t nz = grid->nz, base = nz / n_shards, extra = nz % n_shards;
+    const int64_t zb = shard * base + std::min<int64_t>(shard, extra);
+    *z_begin = (int)zb;
+    *z_end = (int)(zb + base + (shard < extra ? 1 : 0));
+    return GPAIR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// The lattice rows [z0, z1) of a grid-implicit set as a set of its own: the same nodes (the
+// origin moves by z0 spacings, exactly, in double) and amplitudes from row z0 on.
+GaussDev zslab(const GaussDev& g, int z0, int z1, const float* A) {
+    GaussDev s = g;
+    s.nz = z1 - z0;
+    s.oz = g.oz + (double)z0 * (double)g.h;
+    s.A = A + (int64_t)z0 * g.nx * g.ny;
+    s.M = (int64_t)g.nx * g.ny * s.nz;
+    s.ntz = (s.nz + BZ - 1) / BZ;
+    s.ntiles = (int64_t)s.ntx * s.nty * s.ntz;
+    return s;
+}
+
+gpair_status shard_inputs(const gpair_gaussians* gi, const gpair_array* ai, int shard, int n_shards, GaussDev& g,
+                          ArrDev& a, int& z0, int& z1) {
+    gpair_status s = make_gauss(gi, g);
+    if (s != GPAIR_OK) return s;
+    if ((s = make_arr(ai, a)) != GPAIR_OK) return s;
+    if (!g.grid) return GPAIR_ERR_UNSUPPORTED;
+    return gpair_shard_range(gi->grid, shard, n_shards, &z0, &z1);
+}
+}  // namespace
+
+extern "C" {
+
+gpair_status gpair_forward_shard(const gpair_gaussians* gi, const gpair_array* ai, int shard, int n_shards, float* y,
+                                 void* stream) {
+    GaussDev g;
+    ArrDev a;
+    int z0 = 0, z1 = 0;
+    gpair_status s = shard_inputs(gi, ai, shard, n_shards, g, a, z0, z1);
+    if (s != GPAIR_OK) return s;
+    if (!y) return GPAIR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (z1 <= z0)
+        return cuda_status(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)a.Nd * a.Nt, st));
+    const GaussDev gs = zslab(g, z0, z1, gi->A);
+    FwdPlan p = plan_forward_op(gs, a);
+    void* scratch = nullptr;
+    int* status = nullptr;
+    if ((s = get_scratch(st, p.bytes, &scratch, &status)) != GPAIR_OK) return s;
+    return run_forward(gs, a, y, st, scratch, status, p);
+}
+
+gpair_status gpair_adjoint_shard(const gpair_gaussians* gi, const gpair_array* ai, int shard, int n_shards,
+                                 const float* delta, float* gA, void* stream) {
+    GaussDev g;
+    ArrDev a;
+    int z0 = 0, z1 = 0;
+    gpair_status s = shard_inputs(gi, ai, shard, n_shards, g, a, z0, z1);
+    if (s != GPAIR_OK) return s;
+    if (!delta || !gA) return GPAIR_ERR_INVALID_ARG;
+    if (z1 <= z0) return GPAIR_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const GaussDev gs = zslab(g, z0, z1, gi->A);
+    void* scratch = nullptr;
+    const size_t ti_bytes = align256(sizeof(TileInfo) * (size_t)gs.ntiles);
+    const size_t q_bytes = adjoint_q_bytes(gs, a);
+    if ((s = get_scratch(st, ti_bytes + q_bytes, &scratch, nullptr)) != GPAIR_OK) return s;
+    return run_adjoint(gs, a, delta, gA + (int64_t)z0 * g.nx * g.ny, nullptr, nullptr, st, scratch, nullptr,
+                       q_bytes ? static_cast<char*>(scratch) + ti_bytes : nullptr);
+}
+
 gpair_status gpair_voxelize(const gpair_gaussians* gi, const gpair_grid* og, float window_k, float* vol,
                             void* stream) {
     GaussDev g;

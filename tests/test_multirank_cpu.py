@@ -1,11 +1,12 @@
-"""Multi-rank paths on CPU (gloo, world size 2, 127.0.0.1).
+"""Multi-rank paths on CPU (gloo, world sizes 2 and 3, 127.0.0.1).
 
-The GPU path is run as independent replicas (one GPU per process; no collective on the data
-path).  What would shard it -- Gaussians split into z-slabs, partial signals summed over ranks,
-the residual replicated so that each rank's adjoint and Adam step stay local -- is checked here
-on the FP64 oracle: the all-reduced partial forwards equal the full forward and the per-rank
-adjoints are the full adjoint's slices (both operators are sums over Gaussians).  The bench's
-rank helpers and its reference arm under torchrun are exercised the same way.
+The Gaussian-partitioned operator (paper_2602_03893_gb300.sharded: z-slabs from the library's
+gpair_shard_range, partial signals summed by one all-reduce, the residual replicated so that
+each rank's adjoint stays local) is checked here with the FP64 oracle standing in for each
+rank's slab forward: the all-reduced partial forwards equal the full forward and the per-rank
+adjoints over the rank's rows are the full adjoint's slices (both operators are sums over
+Gaussians).  The CUDA kernels behind the same wrapper are checked in tests/test_sharded_gpu.py.
+The bench's rank helpers and its reference arm under torchrun are exercised the same way.
 """
 import json
 import multiprocessing as mp
@@ -41,7 +42,7 @@ def _shard_worker(rank, world, port, q):
         import torch
 
         import oracle
-        from paper_2602_03893_gb300 import synth
+        from paper_2602_03893_gb300 import _lib, sharded, synth
 
         dist = _init(rank, world, port)
         oracle.set_threads(1)
@@ -49,26 +50,38 @@ def _shard_worker(rank, world, port, q):
         A = np.random.default_rng(3).uniform(0.2, 1.0, g.M)
         sens = synth.cap_sensors(9, 8e-3, 160.0)
         v, fs, t0, Nt, k = 1500.0, 40e6, 0.0, 256, 3.0
-        # z-slab of this rank (x fastest, so a z range is a contiguous index range)
-        z0, z1 = rank * g.nz // world, (rank + 1) * g.nz // world
-        lo, hi = z0 * g.nx * g.ny, z1 * g.nx * g.ny
+        grid = _lib.Grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma)
+        gs = _lib.Gaussians(A=torch.as_tensor(A, dtype=torch.float32), grid=grid)
+        arr = _lib.SensorArray(xyz=torch.as_tensor(sens), sound_speed=v, fs=fs, n_samples=Nt, t0=t0, window_k=k)
         G = oracle.gaussians_from_grid(g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.h, g.sigma, A)
-        Gs = oracle.Gaussians(G.c[lo:hi], G.sigma[lo:hi], G.A[lo:hi])
-        y_part = torch.as_tensor(oracle.forward(Gs, sens, v, fs, t0, Nt, k=k))
-        dist.all_reduce(y_part)                      # the one exchange per forward
+
+        def slab(op):
+            r = op.rows
+            return oracle.Gaussians(G.c[r], G.sigma[r], G.A[r])
+
+        def local_forward(y):
+            y.copy_(torch.as_tensor(oracle.forward(slab(op), sens, v, fs, t0, Nt, k=k)))
+
+        op = sharded.ShardedOperator(gs, arr, local_forward=local_forward)
+        y = torch.zeros((len(sens), Nt), dtype=torch.float64)
+        op.forward(y)                                # partial forward + the one all-reduce
         y_full = oracle.forward(G, sens, v, fs, t0, Nt, k=k)
         delta = np.random.default_rng(4).normal(size=y_full.shape)   # replicated residual
-        gA_part = torch.as_tensor(oracle.adjoint(Gs, sens, v, fs, t0, Nt, delta, k=k, want=("A",))["A"])
-        parts = [torch.zeros(((r + 1) * g.nz // world - r * g.nz // world) * g.nx * g.ny, dtype=torch.float64)
-                 for r in range(world)]
-        dist.all_gather(parts, gA_part)
+        gA_part = torch.as_tensor(oracle.adjoint(slab(op), sens, v, fs, t0, Nt, delta, k=k, want=("A",))["A"])
+        sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(sizes, torch.tensor([gA_part.numel()]))
+        nmax = int(max(sizes))          # gloo gathers equal sizes: pad, then trim
+        parts = [torch.zeros(nmax, dtype=torch.float64) for _ in sizes]
+        dist.all_gather(parts, torch.cat([gA_part, torch.zeros(nmax - gA_part.numel(), dtype=torch.float64)]))
+        parts = [p[:int(n)] for p, n in zip(parts, sizes)]
         gA_full = oracle.adjoint(G, sens, v, fs, t0, Nt, delta, k=k, want=("A",))["A"]
-        fwd_err = float(np.linalg.norm(y_part.numpy() - y_full) / np.linalg.norm(y_full))
+        fwd_err = float(np.linalg.norm(y.numpy() - y_full) / np.linalg.norm(y_full))
         adj_err = float(np.linalg.norm(torch.cat(parts).numpy() - gA_full) / np.linalg.norm(gA_full))
+        rows = (op.z_begin, op.z_end)
         dist.destroy_process_group()
-        q.put((rank, fwd_err, adj_err, None))
+        q.put((rank, fwd_err, adj_err, rows, None))
     except Exception as e:   # reported to the parent
-        q.put((rank, None, None, repr(e)))
+        q.put((rank, None, None, None, repr(e)))
 
 
 def _helpers_worker(rank, world, port, q):
@@ -104,10 +117,19 @@ def _run(target, world=2, timeout=240):
     return sorted(out)
 
 
-def test_gaussian_sharded_operators_match_full_operators():
-    for rank, fwd_err, adj_err, err in _run(_shard_worker):
+@pytest.mark.parametrize("world", [2, 3])
+def test_gaussian_sharded_operators_match_full_operators(world):
+    out = _run(_shard_worker, world=world)
+    spans = []
+    for rank, fwd_err, adj_err, rows, err in out:
         assert err is None, err
         assert fwd_err < 1e-13 and adj_err < 1e-13, (rank, fwd_err, adj_err)
+        spans.append(rows)
+    # the slabs tile the 8 lattice rows in order, the first 8 % world ranks one row longer
+    assert spans[0][0] == 0 and spans[-1][1] == 8
+    assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+    assert sorted((e - b for b, e in spans), reverse=True) == [e - b for b, e in spans]
+    assert max(e - b for b, e in spans) - min(e - b for b, e in spans) <= 1
 
 
 def test_bench_rank_helpers():
