@@ -109,18 +109,21 @@ __global__ void slab_info_grid_kernel(GaussDev g, int sbx, int sby, int sbz, int
     si[s] = o;
 }
 
-// SoA mode: bounding box (reference +- radius) and widest sigma of each contiguous tile range.
-__global__ void slab_info_soa_kernel(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, SlabInfo* si) {
+// SoA mode: the axis-aligned box of the Gaussian centres and the widest sigma of each contiguous
+// tile range (exact over the range's Gaussians, so that a slab of elongated tiles keeps a short
+// sample band).
+__global__ void slab_info_soa_kernel(GaussDev g, int64_t ntiles, int64_t tiles_per_slab, SlabInfo* si) {
     __shared__ float red[7][FWD_THREADS / 32];
     const int s = blockIdx.x;
     int64_t tb = s * tiles_per_slab, te = tb + tiles_per_slab;
     if (te > ntiles) te = ntiles;
     float v[7] = {3e38f, 3e38f, 3e38f, 3e38f, 3e38f, 3e38f, 0.f};
-    for (int64_t t = tb + threadIdx.x; t < te; t += blockDim.x) {
-        TileInfo r = ti[t];
-        v[0] = fminf(v[0], r.c0x - r.rad); v[1] = fminf(v[1], r.c0y - r.rad); v[2] = fminf(v[2], r.c0z - r.rad);
-        v[3] = fminf(v[3], -(r.c0x + r.rad)); v[4] = fminf(v[4], -(r.c0y + r.rad)); v[5] = fminf(v[5], -(r.c0z + r.rad));
-        v[6] = fmaxf(v[6], r.smax);
+    const int64_t ie = te * TILE < g.M ? te * TILE : g.M;
+    for (int64_t i = tb * TILE + threadIdx.x; i < ie; i += blockDim.x) {
+        const float x = g.cx[i], y = g.cy[i], z = g.cz[i];
+        v[0] = fminf(v[0], x); v[1] = fminf(v[1], y); v[2] = fminf(v[2], z);
+        v[3] = fminf(v[3], -x); v[4] = fminf(v[4], -y); v[5] = fminf(v[5], -z);
+        v[6] = fmaxf(v[6], g.sg[i]);
     }
     for (int q = 0; q < 6; ++q)
         for (int o = 16; o > 0; o >>= 1) v[q] = fminf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
@@ -135,6 +138,8 @@ __global__ void slab_info_soa_kernel(const TileInfo* ti, int64_t ntiles, int64_t
             float a = red[q][0], b = red[q + 3][0];
             for (int k = 1; k < nw; ++k) { a = fminf(a, red[q][k]); b = fminf(b, red[q + 3][k]); }
             o.lo[q] = a; o.hi[q] = -b;
+            const float pad = 1e-6f * (fabsf(o.lo[q]) + fabsf(o.hi[q])) + 1e-9f;   // rounding slack
+            o.lo[q] -= pad; o.hi[q] += pad;
         }
         float sm = red[6][0];
         for (int k = 1; k < nw; ++k) sm = fmaxf(sm, red[6][k]);
@@ -1076,9 +1081,9 @@ cudaError_t launch_slab_info_grid(const GaussDev& g, int sbx, int sby, int sbz, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
+cudaError_t launch_slab_info_soa(const GaussDev& g, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
                                  cudaStream_t st) {
-    slab_info_soa_kernel<<<S, FWD_THREADS, 0, st>>>(ti, ntiles, tiles_per_slab, si);
+    slab_info_soa_kernel<<<S, FWD_THREADS, 0, st>>>(g, ntiles, tiles_per_slab, si);
     return cudaGetLastError();
 }
 
@@ -1130,6 +1135,18 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
         fwd_slab_kernel<false><<<grid, FWD_THREADS, smem, st>>>(g, a, ti, si, partial, rows, PL, LB, TB, banded,
                                                                 status, 0, null_tmap());
     }
+    return cudaGetLastError();
+}
+
+// Banded rows (start sample, length; row capacity PL) of any Gaussian set.
+cudaError_t launch_slab_reduce_rows(const ArrDev& a, const float* partial, const int2* rows, int S, int PL, float* y,
+                                    cudaStream_t st) {
+    dim3 rgrid((a.Nt + 255) / 256, a.Nd);
+    if (S <= SLAB_RED_MAX_S)
+        slab_reduce_banded_kernel<<<rgrid, SLAB_RED_THREADS, (size_t)S * sizeof(int2), st>>>(partial, rows, S, a.Nd,
+                                                                                             a.Nt, PL, y);
+    else
+        slab_reduce_kernel<<<rgrid, 256, 0, st>>>(partial, rows, S, a.Nd, a.Nt, PL, 1, y);
     return cudaGetLastError();
 }
 

@@ -16,13 +16,18 @@
 namespace gp {
 cudaError_t launch_tile_info(const GaussDev& g, TileInfo* ti, cudaStream_t st);
 cudaError_t launch_slab_info_grid(const GaussDev& g, int sbx, int sby, int sbz, int S, SlabInfo* si, cudaStream_t st);
-cudaError_t launch_slab_info_soa(const TileInfo* ti, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
+cudaError_t launch_slab_info_soa(const GaussDev& g, int64_t ntiles, int64_t tiles_per_slab, int S, SlabInfo* si,
                                  cudaStream_t st);
 cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
                            float* partial, int2* rows, int PL, int LB, int TB, bool binned, int* status,
                            const CUtensorMap* tmap, const MomentTable* mom, cudaStream_t st);
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
+size_t fwd_free_smem(int NW, int LB);
+cudaError_t launch_forward_free(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
+                                float* partial, int2* rows, int PL, int LB, int NW, cudaStream_t st);
+cudaError_t launch_slab_reduce_rows(const ArrDev& a, const float* partial, const int2* rows, int S, int PL, float* y,
+                                    cudaStream_t st);
 size_t fwd_lanes_smem(int NW, int NZ, int LB, int P, int L);
 int fwd_lanes_nz(float h, float invDelta);
 cudaError_t launch_slab_info_cubes(const GaussDev& g, int scx, int scy, int scz, int S, SlabInfo* si, cudaStream_t st);
@@ -216,7 +221,8 @@ struct FwdPlan {
     int PL;                // partial row length
     bool binned;           // grid mode: per-(tile, sensor) binned kernel
     bool lanes;            // grid mode: the sensor-lane moment kernel (slabs of 8^3-node cubes)
-    int NW, NZ;            // its warps per CTA and moment-band bins
+    bool free_lanes;       // SoA mode: the sensor-lane direct kernel (slabs of tile ranges)
+    int NW, NZ;            // warps per CTA of the lanes kernels; moment-band bins (grid)
     size_t off_ti, off_si, off_rows, off_part, bytes;
 };
 
@@ -390,12 +396,39 @@ bool plan_forward_lanes(const GaussDev& g, const ArrDev& a, const MomentTable& T
     return true;
 }
 
-// The operator's plan: the sensor-lane kernel where the expansion applies and its bands fit,
-// else the brick (grid) or tile-range (free centres) plan.
+constexpr int FREE_LANES_WARPS = 4;    // warps (sensor groups of 32) per CTA of the free-centre kernel
+
+// Free-centre Gaussians with the sensor-lane direct kernel: slabs of contiguous tile ranges,
+// enough of them for about four CTAs per SM while the partial rows (capacity N_t, rounded up to
+// 4, per slab and sensor) stay within 2 GB; the shared signal band per warp as long as 227 KB
+// allow (a sensor whose slab band is longer takes several passes).
+bool plan_forward_free(const GaussDev& g, const ArrDev& a, FwdPlan& p) {
+    memset(&p, 0, sizeof(p));
+    p.NW = std::min(FREE_LANES_WARPS, (a.Nd + 31) / 32);
+    const int groups = (a.Nd + 32 * p.NW - 1) / (32 * p.NW);
+    int64_t S = ((int64_t)device_sms() * 4 + groups - 1) / groups;
+    if (S > g.ntiles) S = g.ntiles;
+    p.PL = (a.Nt + 3) & ~3;
+    const int64_t row = (int64_t)a.Nd * p.PL * 4;
+    while (S > 1 && S * row > ((int64_t)2 << 30)) S = (S + 1) / 2;
+    if (S < 1 || S > 65535) return false;
+    p.tiles_per_slab = (g.ntiles + S - 1) / S;
+    p.S = (int)((g.ntiles + p.tiles_per_slab - 1) / p.tiles_per_slab);
+    const size_t per_warp = (SMEM_PER_CTA - fwd_free_smem(0, 0)) / p.NW;
+    p.LB = std::min<int64_t>(p.PL, (int64_t)(per_warp / (32 * 4)) & ~(int64_t)3);
+    if (p.LB < 64) return false;
+    p.free_lanes = true;
+    plan_offsets(p, g, a);
+    return true;
+}
+
+// The operator's plan: the sensor-lane kernels where they apply (grid: the expansion and its
+// bands fit; free centres: always), else the brick (grid) or tile-range (free centres) plan.
 FwdPlan plan_forward_op(const GaussDev& g, const ArrDev& a) {
     MomentTable T;
     FwdPlan p;
     if (g.grid && make_moment_table(g, a, T) && plan_forward_lanes(g, a, T, p)) return p;
+    if (!g.grid && plan_forward_free(g, a, p)) return p;
     return plan_forward(g, a);
 }
 
@@ -437,6 +470,15 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     cudaError_t e = cudaSuccess;
+    if (p.free_lanes) {
+        e = launch_tile_info(g, ti, st);
+        if (e == cudaSuccess) e = launch_slab_info_soa(g, g.ntiles, p.tiles_per_slab, p.S, si, st);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) e = launch_forward_free(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.NW, st);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = launch_slab_reduce_rows(a, part, rows, p.S, p.PL, y, st);
+        return cuda_status(e);
+    }
     if (p.lanes) {
         MomentTable mom;
         if (!make_moment_table(g, a, mom)) return GPAIR_ERR_UNSUPPORTED;
@@ -455,7 +497,7 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
         e = launch_slab_info_grid(g, p.sbx, p.sby, p.sbz, p.S, si, st);
     } else {
         e = launch_tile_info(g, ti, st);
-        if (e == cudaSuccess) e = launch_slab_info_soa(ti, g.ntiles, p.tiles_per_slab, p.S, si, st);
+        if (e == cudaSuccess) e = launch_slab_info_soa(g, g.ntiles, p.tiles_per_slab, p.S, si, st);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
     MomentTable mom;

@@ -127,3 +127,19 @@ def test_deterministic_given_inputs_up_to_atomic_order():
     y1 = gpu_forward(w)
     y2 = gpu_forward(w)
     assert rel_l2(y1, y2) < 1e-6
+
+
+def test_free_gaussians_band_longer_than_shared_memory():
+    """Free Gaussians scattered through an 80 mm cube and sensors 200 mm away: a sensor's samples
+    for one slab (2000 to 3700) outnumber the shared signal band (1684 with one warp), so the
+    sensor-lane kernel takes two or three passes over each slab, each keeping its own samples (windows
+    that lie wholly in another pass's samples add nothing to this one)."""
+    rng = np.random.default_rng(21)
+    n = 1024
+    c = rng.uniform(-40e-3, 40e-3, (3, n))
+    free = tuple(np.ascontiguousarray(q, dtype=np.float32) for q in
+                 (c[0], c[1], c[2], np.exp(rng.uniform(np.log(0.05e-3), np.log(0.2e-3), n)), rng.uniform(0.2, 1.0, n)))
+    g = synth.centred_grid(8, 8, 16, 0.1e-3)      # only its size is used: M = 1024
+    w = synth.Workload("free-spread", g, synth.cap_sensors(8, 200e-3, 120.0), 8192, free=free)
+    rel, y, yo = _check(w)
+    assert np.abs(yo).max() > 0
