@@ -127,7 +127,7 @@ def diff_leg(args, dev, stream, p_fp32, p_mufu, pipe_peaks, world):
     """The differentiation workload: 262,144 free Gaussians (64^3 lattice jittered by U[+-0.05] mm,
     sigma log-uniform 0.05-0.2 mm), 512 sensors x 2048 samples.  Amplitudes dense (U[0,1]^2, as
     an optimisation iterate has them).  Times gpair_forward (free centres: tile and slab summaries,
-    fwd_slab_kernel, slab reduction) and gpair_adjoint with all three gradients (tile summaries,
+    fwd_free_lanes_kernel, slab reduction) and gpair_adjoint with all three gradients (tile summaries,
     adj_kernel with the centre and width derivatives) on the stream, CUDA events, after warm-up."""
     import torch
 
@@ -167,7 +167,7 @@ def diff_leg(args, dev, stream, p_fp32, p_mufu, pipe_peaks, world):
                              FULL_MUFU_PER_SAMPLE * samples + FULL_MUFU_PER_PAIR * pairs)}
     out = {"workload": w.name, "gaussians": w.M, "sensors": w.Nd, "samples": w.Nt, "pairs": pairs,
            "sample_evals": samples, "amplitudes": "dense U[0,1]^2", "reps": reps,
-           "kernels": {"forward": "fwd_slab_kernel", "adjoint_full": "adj_kernel (A, c, sigma)"}}
+           "kernels": {"forward": "fwd_free_lanes_kernel", "adjoint_full": "adj_kernel (A, c, sigma)"}}
     for name, (F, X) in work.items():
         tm = times[name]
         t_fp32, t_mufu = F / p_fp32, X / p_mufu
@@ -177,7 +177,7 @@ def diff_leg(args, dev, stream, p_fp32, p_mufu, pipe_peaks, world):
         out[name] = {"ms": tm * 1e3, "alg_fp32_ops": F, "alg_mufu_ops": X, "bound_pipe": pipe,
                      "achieved": ops / tm / 1e12, "peak": peak / 1e12, "frac": ops / tm / peak,
                      "frac_of_measured": ops / tm / pm, "pair_evals_per_s": pairs / tm,
-                     "includes": ("tile and slab summaries + fwd_slab_kernel + slab reduction" if name == "forward"
+                     "includes": ("tile and slab summaries + fwd_free_lanes_kernel + slab reduction" if name == "forward"
                                   else "tile summaries + adj_kernel with centre and width gradients")}
     return out
 
