@@ -186,7 +186,9 @@ __global__ void slab_info_cube_kernel(GaussDev g, int ncx, int ncy, int ncz, int
 constexpr float FL_MAGIC = 12582912.0f;
 constexpr int FL_MAGIC_BITS = 0x4B400000;
 
-template <int P>
+// LF > 0: the correlation for windows of at most LF positions with the outputs in a register
+// ring of LF (the table's coefficients are compile-time operands); LF = 0: any window length.
+template <int P, int LF>
 __global__ void __launch_bounds__(FL_MAXW * 32, 1)
 fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float* __restrict__ partial,
                  int2* __restrict__ rows, int LB, int NZ, int* status, int use_tma,
@@ -378,6 +380,41 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last && t + FL_RING < nCubes) fill(t + FL_RING);
         if (active) {
+        if constexpr (LF > 0) {
+        // correlation of the cube's moment band into the signal band, bin by bin: bin b adds
+        // c[m] . Z[b] to output b + m for m < LF; acc[s] holds the output n with n = s (mod LF),
+        // and output b is complete once bin b is in.  Each bin is cleared as it is read.
+        float acc[LF];
+#pragma unroll
+        for (int q = 0; q < LF; ++q) acc[q] = 0.f;
+        for (int b0 = 0; b0 < NZ; b0 += LF) {
+#pragma unroll
+            for (int bb = 0; bb < LF; ++bb) {
+                const int b = b0 + bb;
+                if (b >= NZ) break;
+                float z[8];
+                Z.load(b * 32 + lane, z);
+                Z.clear(b * 32 + lane);
+#pragma unroll
+                for (int m = 0; m < LF; ++m) {
+                    float v = acc[(bb + m) & (LF - 1)];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) v = fmaf(T.c[m][p], z[p], v);
+                    acc[(bb + m) & (LF - 1)] = v;
+                }
+                const int yi = yoff + b;
+                if ((unsigned)yi < (unsigned)LBe) Y[yi * 32 + lane] += acc[bb];
+                acc[bb] = 0.f;
+            }
+        }
+        // outputs NZ .. NZ + L - 2 are still in their slots
+#pragma unroll
+        for (int q = 0; q < LF; ++q) {
+            const int n = NZ + ((q - NZ) & (LF - 1));
+            const int yi = yoff + n;
+            if (n < NO && (unsigned)yi < (unsigned)LBe) Y[yi * 32 + lane] += acc[q];
+        }
+        } else {
         // correlation of the cube's moment band into the signal band, FL_Q outputs at a time:
         // acc[q] = sum_m c[m] . Z[c0 + q - m]; a ring of FL_Q bins in registers, slot (q - m) mod FL_Q
         for (int c0 = 0; c0 < NO; c0 += FL_Q) {
@@ -423,6 +460,7 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         }
         for (int i = 0; i < NZ; ++i) Z.clear(i * 32 + lane);
         }
+        }
     }
     if (!ok && lane == 0) {   // a bounded wait ran out
         set_status(status, DEV_TIMEOUT);
@@ -464,7 +502,10 @@ cudaError_t launch_forward_lanes(const GaussDev& g, const ArrDev& a, const SlabI
     static const CUtensorMap zero_map = [] { CUtensorMap z; memset(&z, 0, sizeof(z)); return z; }();
     const size_t smem = fl_smem_bytes(NW, NZ, LB, T.P, T.L);
     dim3 grid((a.Nd + 32 * NW - 1) / (32 * NW), S);
-    auto kern = T.P == 6 ? fwd_lanes_kernel<6> : (T.P == 7 ? fwd_lanes_kernel<7> : fwd_lanes_kernel<8>);
+    const bool l16 = T.L <= 16;     // the table is zero beyond L: a 16-slot ring serves any L <= 16
+    auto kern = T.P == 6 ? (l16 ? fwd_lanes_kernel<6, 16> : fwd_lanes_kernel<6, 0>)
+              : T.P == 7 ? (l16 ? fwd_lanes_kernel<7, 16> : fwd_lanes_kernel<7, 0>)
+                         : (l16 ? fwd_lanes_kernel<8, 16> : fwd_lanes_kernel<8, 0>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 32 * NW, smem, st>>>(g, a, si, partial, rows, LB, NZ, status, tmap != nullptr,
