@@ -311,61 +311,79 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         }
         const float* tile = S.tileA[b];
         unsigned relmax = 0;       // largest band offset of the cube's pairs (as unsigned: negatives too)
-        if (active) {
+        // a cube without amplitudes adds nothing (sparse images): the warp skips it
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < CUBE_N / 32 / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(tile)[lane * (CUBE_N / 32 / 4) + q];
+            any |= (v.x != 0.f) | (v.y != 0.f) | (v.z != 0.f) | (v.w != 0.f);
+        }
+        const bool cube_on = __any_sync(0xffffffffu, any);
+        // The pairs of lattice row `row` (= 8 lz + ly, 8 Gaussians along x) without branches: their
+        // moments, band slots and the row's extreme e on the edge's side.
+        auto row_pairs = [&](int row, float (&mom)[CUBE][P], int (&idx)[CUBE], float (&ev)[CUBE], float& eext) {
+            const int lz = row >> 3, ly = row & (CUBE - 1);
+            const float4 a0 = *reinterpret_cast<const float4*>(tile + row * CUBE);
+            const float4 a1 = *reinterpret_cast<const float4*>(tile + row * CUBE + 4);
+            const float Arow[CUBE] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float oy = ((float)ly - 0.5f * (CUBE - 1)) * h, oz = ((float)lz - 0.5f * (CUBE - 1)) * h;
+            const float ayz = fmaf(oy, fmaf(2.f, r.v0y, oy), oz * fmaf(2.f, r.v0z, oz));
+            eext = edge_in ? 3.f : -3.f;
+#pragma unroll
+            for (int lx = 0; lx < CUBE; ++lx) {
+                const float num = ax[lx] + ayz;
+                float invR, phi;
+                pair_phase_num(r, num, invR, phi);
+                const float tt = fmaf(phi, invDelta, -ksi);      // window start: first d <= k sigma
+                const float u = __fadd_ru(tt, magk);              // magk + ceil(tt)
+                const float mf = u - magk;
+                const int rel = __float_as_int(u) - FL_MAGIC_BITS;   // ceil(tt) - fl0
+                const float d0 = fmaf(-mf, Delta, phi);
+                const float e = (d0 - T.dstar) * T.inv_half;
+                // rel lies in [0, NZ) by the band's bound; a clamp keeps any other value inside the
+                // band, and the kernel then reports the capacity status
+                const unsigned ur = (unsigned)rel;
+                relmax = max(relmax, ur);
+                idx[lx] = (int)min(ur, (unsigned)(NZ - 1)) * 32 + lane;
+                mom[lx][0] = Arow[lx] * invR;                      // the table carries the 1/2
+#pragma unroll
+                for (int p = 1; p < P; ++p) mom[lx][p] = mom[lx][p - 1] * e;
+                ev[lx] = e;
+                eext = edge_in ? fminf(eext, e) : fmaxf(eext, e);
+            }
+        };
+        if (active && cube_on) {
+            // Software pipeline over the cube's 64 rows, two per step: the next row's pairs are
+            // formed while the current row's read-modify-writes (a chain through shared memory)
+            // are in flight.  Rows needing the edge correction are marked and redone afterwards.
+            float momA[CUBE][P], momB[CUBE][P], evA[CUBE], evB[CUBE], eA, eB;
+            int idxA[CUBE], idxB[CUBE];
+            unsigned long long emask = 0;
+            row_pairs(0, momA, idxA, evA, eA);
 #pragma unroll 1
-            for (int lz = 0; lz < CUBE; ++lz) {
-                const float oz = ((float)lz - 0.5f * (CUBE - 1)) * h;
-                const float azv = oz * fmaf(2.f, r.v0z, oz);
-#pragma unroll 1
-                for (int ly = 0; ly < CUBE; ++ly) {
-                    const float4 a0 = *reinterpret_cast<const float4*>(tile + (lz * CUBE + ly) * CUBE);
-                    const float4 a1 = *reinterpret_cast<const float4*>(tile + (lz * CUBE + ly) * CUBE + 4);
-                    if (a0.x == 0.f && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f &&
-                        a1.z == 0.f && a1.w == 0.f)
-                        continue;
-                    const float Arow[CUBE] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    const float oy = ((float)ly - 0.5f * (CUBE - 1)) * h;
-                    const float ayz = fmaf(oy, fmaf(2.f, r.v0y, oy), azv);
-                    // the row's 8 pairs without branches: moments, band slots and the edge flags
-                    float mom[CUBE][P], ev[CUBE];
-                    int idx[CUBE];
-                    float eext = edge_in ? 3.f : -3.f;     // extreme e of the row on the edge's side
+            for (int row = 0; row < CUBE * CUBE; row += 2) {
+                row_pairs(row + 1, momB, idxB, evB, eB);
 #pragma unroll
-                    for (int lx = 0; lx < CUBE; ++lx) {
-                        const float num = ax[lx] + ayz;
-                        float invR, phi;
-                        pair_phase_num(r, num, invR, phi);
-                        const float tt = fmaf(phi, invDelta, -ksi);      // window start: first d <= k sigma
-                        const float u = __fadd_ru(tt, magk);              // magk + ceil(tt)
-                        const float mf = u - magk;
-                        const int rel = __float_as_int(u) - FL_MAGIC_BITS;   // ceil(tt) - fl0
-                        const float d0 = fmaf(-mf, Delta, phi);
-                        const float e = (d0 - T.dstar) * T.inv_half;
-                        // rel lies in [0, NZ) by the band's bound; a clamp keeps any other value inside
-                        // the band, and the kernel then reports the capacity status
-                        const unsigned ur = (unsigned)rel;
-                        relmax = max(relmax, ur);
-                        idx[lx] = (int)min(ur, (unsigned)(NZ - 1)) * 32 + lane;
-                        mom[lx][0] = Arow[lx] * invR;                      // the table carries the 1/2
+                for (int k = 0; k < CUBE; k += 2) Z.add2(idxA[k], idxA[k + 1], momA[k], momA[k + 1]);
+                emask |= (unsigned long long)edge_corrected(T, eA) << row;
+                row_pairs((row + 2) & (CUBE * CUBE - 1), momA, idxA, evA, eA);   // row 64: a dummy row 0
 #pragma unroll
-                        for (int p = 1; p < P; ++p) mom[lx][p] = mom[lx][p - 1] * e;
-                        ev[lx] = e;
-                        eext = edge_in ? fminf(eext, e) : fmaxf(eext, e);
+                for (int k = 0; k < CUBE; k += 2) Z.add2(idxB[k], idxB[k + 1], momB[k], momB[k + 1]);
+                emask |= (unsigned long long)edge_corrected(T, eB) << (row + 1);
+            }
+            // edge position E (rare at the benchmark's geometry): the direct term of the marked rows
+            while (emask) {
+                const int row = __ffsll(emask) - 1;
+                emask &= emask - 1;
+                row_pairs(row, momA, idxA, evA, eA);
+#pragma unroll
+                for (int lx = 0; lx < CUBE; ++lx)
+                    if (edge_corrected(T, evA[lx])) {
+                        const float dE = fmaf(evA[lx], 0.5f * Delta, T.dstar) - ED;   // d0 - E Delta
+                        const int yi = yoff + (idxA[lx] >> 5) + T.E;
+                        if ((unsigned)yi < (unsigned)LBe)
+                            Y[yi * 32 + lane] += efac * momA[lx][0] * dE * ex2_approx(dE * dE * c2);
                     }
-#pragma unroll
-                    for (int k = 0; k < CUBE; k += 2) Z.add2(idx[k], idx[k + 1], mom[k], mom[k + 1]);
-                    // edge position E (rare at the benchmark's geometry): the direct term
-                    if (edge_corrected(T, eext)) {
-#pragma unroll
-                        for (int lx = 0; lx < CUBE; ++lx)
-                            if (edge_corrected(T, ev[lx])) {
-                                const float dE = fmaf(ev[lx], 0.5f * Delta, T.dstar) - ED;   // d0 - E Delta
-                                const int yi = yoff + (idx[lx] >> 5) + T.E;
-                                if ((unsigned)yi < (unsigned)LBe)
-                                    Y[yi * 32 + lane] += efac * mom[lx][0] * dE * ex2_approx(dE * dE * c2);
-                            }
-                    }
-                }
             }
         }
         if (relmax >= (unsigned)NZ) set_status(status, DEV_CAPACITY);   // a pair outside its band: not reached
@@ -379,7 +397,7 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         }
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last && t + FL_RING < nCubes) fill(t + FL_RING);
-        if (active) {
+        if (active && cube_on) {
         if constexpr (LF > 0) {
         // correlation of the cube's moment band into the signal band, bin by bin: bin b adds
         // c[m] . Z[b] to output b + m for m < LF; acc[s] holds the output n with n = s (mod LF),
