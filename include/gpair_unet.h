@@ -29,10 +29,11 @@ extern "C" {
 typedef uint16_t gpair_bf16;
 
 /* Convolution path of gpair_conv3d_fwd / _dgrad.  The 5th-generation tensor-core kernel (tcgen05
- * MMAs, accumulator in tensor memory) takes shapes with Cin and Cout multiples of 16, Cout <= 128
- * or a multiple of 128, and 16-byte aligned tensors.  Mode 1 (default) uses it for Cout >= 64,
- * where it measured faster than the mma.sync kernel; mode 2 for every eligible shape; mode 0
- * never.  Other values only query.  Returns the mode in force. */
+ * MMAs with accumulators in tensor memory, operands loaded by TMA) takes shapes with Cin and Cout
+ * multiples of 16, 1 or 27 taps and 16-byte aligned tensors.  Mode 1 (default) uses it for every
+ * eligible shape and the mma.sync kernel for the others; mode 2 uses it alone (an ineligible shape
+ * returns GPAIR_ERR_UNSUPPORTED); mode 0 uses the mma.sync kernel alone.  Other values only
+ * query.  Returns the mode in force. */
 int gpair_unet_tensor_path(int mode);
 /* 1 if a bounded wait of the tensor-core convolution gave up since the last call (then cleared). */
 int gpair_unet_tc_status(void);

@@ -377,8 +377,8 @@ gpair_status st(cudaError_t e) { return e == cudaSuccess ? GPAIR_OK : GPAIR_ERR_
 
 bool dims_ok(int D, int H, int W, int C) { return D > 0 && H > 0 && W > 0 && C > 0; }
 
-// 1: tcgen05 kernel for Cout >= 64 (where it measured faster); 2: tcgen05 for every eligible
-// shape; 0: mma.sync kernel only.
+// 1: the tcgen05 kernel for every eligible shape, the mma.sync kernel for the others; 2: the
+// tcgen05 kernel only (an ineligible shape is GPAIR_ERR_UNSUPPORTED); 0: the mma.sync kernel only.
 int g_tensor_path = 1;
 
 }  // namespace
@@ -403,12 +403,14 @@ gpair_status gpair_conv3d_fwd(const gpair_bf16* in, int D, int H, int W, int Cin
     if (!in || !w || !out || !dims_ok(D, H, W, Cin) || Cout <= 0 || (taps != 1 && taps != 27)) return GPAIR_ERR_INVALID_ARG;
     if (Cin % 16 != 0 || Cout % 8 != 0) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (g_tensor_path == 2 || (g_tensor_path == 1 && Cout >= 64)) {
+    if (g_tensor_path != 0) {
         const cudaError_t e = gp::launch_conv3d_fwd_tc(reinterpret_cast<const uint16_t*>(in), D, H, W, Cin,
                                                        reinterpret_cast<const uint16_t*>(w), bias, Cout, taps, relu,
                                                        reinterpret_cast<uint16_t*>(out), s);
         if (e != cudaErrorNotSupported) return st(e);
-        cudaGetLastError();     // not eligible: the mma.sync kernel below
+        cudaGetLastError();
+        if (g_tensor_path == 2) return GPAIR_ERR_UNSUPPORTED;
+        // not eligible: the mma.sync kernel below
     }
     const int64_t nv = (int64_t)D * H * W;
     const unsigned gx = (unsigned)((nv + 16 * CONV_MT * 4 - 1) / (16 * CONV_MT * 4));

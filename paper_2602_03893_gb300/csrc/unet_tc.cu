@@ -1,18 +1,25 @@
 // unet_tc.cu -- the U-Net's 3-D convolution as an implicit GEMM on the 5th-generation tensor
-// cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// cores (tcgen05.mma kind::f16: BF16 operands, FP32 accumulators in tensor memory), fed by TMA.
 //
-// GEMM view: rows are output voxels, columns output channels, the reduction runs over
-// (tap, input channel).  CTA = 128 consecutive output voxels (the 128 TMEM lanes of the
-// accumulator) x NT output channels (NT columns of TMEM), four warps.  The reduction is cut into
-// stages of one tap and Kc input channels; each stage's operand tiles are gathered into shared
-// memory (A: the voxels' shifted input rows, zero where the tap falls outside the volume; B: the
-// weights' rows) with cp.async, in the canonical K-major layout without swizzle (core matrices of
-// 8 rows x 16 bytes; adjacent core matrices along K are 128 bytes apart, along M/N Kc * 16 bytes).
-// One thread issues the stage's MMAs (K = 16 each) and commits them to the stage buffer's
-// mbarrier; the gathers of the next stages, in a ring of shared buffers, overlap them.  Every wait
-// is bounded.
-// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31),
-// adds the bias, applies the ReLU and stores BF16.
+// Tile: 8 (x) x 16 (y) x ZT (z) output voxels and NT output channels.  One MMA takes the 128
+// voxels of one z-slice of the tile (8 x 16) as its rows, the NT channels as its columns and 16
+// input channels of one tap as its K.  The CTA stages the tile's input halo (for a 3 x 3 x 3
+// stencil 10 x 18 x (ZT + 2) voxels, KC channels) with one TMA load in the layout
+// [8-channel chunk][z][y][x][8 channels]: the 8 rows of a core matrix (8 voxels consecutive in x,
+// 16 bytes each) are contiguous, so the operand of tap (dz, dy, dx) and slice zs is the same
+// K-major layout starting ((zs + dz) 18 + dy) 10 + dx rows further in.  Shifting the descriptor
+// replaces the im2col copy; the zero padding is the TMA's out-of-range fill.  The weights of the
+// stage (taps x NT x KC) arrive by a second TMA load as [tap][8-channel chunk][co][8].  When one
+// stage holds every input channel, the weights are loaded once per CTA and stay resident.
+//
+// Warp roles of the persistent CTA: warp 0 issues the TMA loads into a ring of stages, warp 1
+// owns tensor memory and issues the MMAs (one thread), warps 2-5 drain the accumulators
+// (tcgen05.ld; warp w reads TMEM lanes 32 (w mod 4) ...), add the bias, apply the ReLU and store
+// BF16.  Two accumulator buffers in tensor memory let the epilogue of one tile overlap the MMAs of
+// the next.  Every wait is bounded; after a wait gives up, its warp sets the status word and
+// skips its remaining waits, so the CTA runs to its end.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,20 +29,17 @@
 
 namespace gp {
 
-constexpr int TC_M = 128;          // voxels per CTA = accumulator lanes
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 192;      // 6 warps: TMA, MMA, 4 x epilogue
+constexpr int TC_TX = 8, TC_TY = 16; // tile extent in x and y: 128 GEMM rows per z-slice
+constexpr int TC_MAX_STAGES = 4;
+constexpr size_t TC_SMEM_MAX = 227 * 1024;
 
-__device__ int g_conv_tc_status;   // 1: a bounded wait gave up
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
+__device__ int g_conv_tc_status;     // 1: a bounded wait gave up
 
 // Shared-memory matrix descriptor, no swizzle: start address, leading (K) and stride (M/N) byte
 // offsets in 16-byte units, descriptor version 1 at bits 46-47, layout type 0.
-__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo_bytes, uint32_t sbo_bytes) {
-    uint64_t d = (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu);
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
@@ -73,142 +77,325 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        ::"r"(dst), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ uint16_t f2bf_rn(float f) {
     const __nv_bfloat16 h = __float2bfloat16_rn(f);
     return *reinterpret_cast<const uint16_t*>(&h);
 }
 
-// out[v][co0 + c] = act(bias + sum_{t, ci} in[v + off(t)][ci] w[co0 + c][t][ci]), c < NT.
-// TC_STAGES shared buffers: the gathers of up to TC_STAGES - 1 stages are in flight (one cp.async
-// group each) while the tensor cores work; a buffer is refilled once the commit of the MMAs that
-// read it has arrived on its mbarrier.
-constexpr int TC_STAGES = 4;
+struct ConvTcArgs {
+    int D, H, W, Cout;
+    int NT, ZT, KC, nK;             // channel tile, z-slices per tile, channels per stage, stages per tile
+    int tiles_x, tiles_y, n_tiles;  // spatial tiles along x and y, channel tiles
+    int64_t units;                  // spatial tiles x channel tiles
+    int nstages;                    // ring depth
+    uint32_t a_bytes, a_stride;     // halo box bytes, and its slot size (128-byte multiple)
+    uint32_t b_bytes;               // weight box bytes
+    uint32_t tmem_cols;
+    int b_resident;                 // nK == 1: weights loaded once per CTA
+    int relu;
+    const float* bias;
+    uint16_t* out;
+};
 
-__global__ void __launch_bounds__(TC_THREADS)
-conv3d_fwd_tc_kernel(const uint16_t* __restrict__ in, int D, int H, int W, int Cin, const uint16_t* __restrict__ w,
-                     const float* __restrict__ bias, int Cout, int NT, int ncols, int taps, int relu, int Kc,
-                     uint16_t* __restrict__ out) {
+// Shared memory: [ring of stages: halo (a_stride) + weights (b_bytes, unless resident)]
+// [resident weights] [barriers: full, empty per stage; acc_full, acc_empty x 2; weights] [tmem slot]
+template <int TAPS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const ConvTcArgs p) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t nv = (int64_t)D * H * W;
-    const int64_t v = (int64_t)blockIdx.x * TC_M + tid;     // this thread's voxel row (A) and TMEM lane
-    const int co0 = blockIdx.y * NT;
-    const int K = taps * Cin;
-    const uint32_t aBytes = (uint32_t)TC_M * Kc * 2, bBytes = (uint32_t)NT * Kc * 2;
-    const uint32_t stBytes = aBytes + bBytes;               // stage buffer: A tile then B tile
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + TC_STAGES * stBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES);
-    const uint32_t lbo = 128, sbo = (uint32_t)(Kc / 8) * 128;
+    constexpr int R = TAPS == 27 ? 1 : 0;                 // halo width
+    constexpr int HX = TC_TX + 2 * R, HY = TC_TY + 2 * R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = p.nstages;
+    const uint32_t stage_bytes = p.a_stride + (p.b_resident ? 0u : p.b_bytes);
+    unsigned char* bres = sm + (size_t)NS * stage_bytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bres + (p.b_resident ? p.b_bytes : 0u));
+    uint64_t* empty = full + TC_MAX_STAGES;
+    uint64_t* acc_full = empty + TC_MAX_STAGES;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* wbar = acc_empty + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(ncols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int q = 0; q < TC_STAGES; ++q) mbar_init(&mbar[q], 1);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+        for (int q = 0; q < 2; ++q) { mbar_init(&acc_full[q], 1); mbar_init(&acc_empty[q], 4); }
+        mbar_init(wbar, 1);
         fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    const bool vok = v < nv;
-    const int64_t vv = vok ? v : 0;
-    const int vx = (int)(vv % W), vy = (int)((vv / W) % H), vz = (int)(vv / ((int64_t)W * H));
-    const int nchunk = Cin / Kc, S = taps * nchunk;
-    const uint32_t idesc = tc_idesc(NT, TC_M);
     bool ok = true;
+    const int ntile_xy = p.tiles_x * p.tiles_y;
 
-    // gather stage s into its buffer (one cp.async group; empty groups past the last stage keep
-    // the group count uniform)
-    auto gather = [&](int s) {
-        if (s < S) {
-            unsigned char* buf = sm + (s % TC_STAGES) * stBytes;
-            const int t = s / nchunk, c0 = (s - t * nchunk) * Kc;
-            int dz = 0, dy = 0, dx = 0;
-            if (taps == 27) { dz = t / 9 - 1; dy = (t / 3) % 3 - 1; dx = t % 3 - 1; }
-            const int x = vx + dx, y = vy + dy, z = vz + dz;
-            const bool inb = vok && x >= 0 && x < W && y >= 0 && y < H && z >= 0 && z < D;
-            const uint16_t* asrc = inb ? in + (((int64_t)z * H + y) * W + x) * Cin + c0 : in;
-            unsigned char* arow = buf + (tid >> 3) * sbo + (tid & 7) * 16;
-            for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(arow + kc * 128, asrc + kc * 8, inb ? 16u : 0u);
-            for (int r = tid; r < NT; r += TC_THREADS) {
-                const uint16_t* bsrc = w + (int64_t)(co0 + r) * K + (int64_t)t * Cin + c0;
-                unsigned char* brow = buf + aBytes + (r >> 3) * sbo + (r & 7) * 16;
-                for (int kc = 0; kc < Kc / 8; ++kc) cp_async16(brow + kc * 128, bsrc + kc * 8, 16u);
+    if (warp == 0) {
+        // ---- TMA producer
+        if (lane == 0) {
+            if (p.b_resident) {
+                mbar_arrive_expect_tx(wbar, p.b_bytes);
+                tma_load_4d(smem_u32(bres), &tmB, 0, 0, 0, 0, wbar);     // n_tiles == 1 when resident
+            }
+            int s = 0;
+            uint32_t ph = 0;
+            for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+                const int nt = (int)(u % p.n_tiles);
+                const int64_t st = u / p.n_tiles;
+                const int tx = (int)(st % p.tiles_x), ty = (int)((st / p.tiles_x) % p.tiles_y);
+                const int tz = (int)(st / ntile_xy);
+                for (int k = 0; k < p.nK; ++k) {
+                    if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
+                    const uint32_t dst = smem_u32(sm + (size_t)s * stage_bytes);
+                    mbar_arrive_expect_tx(&full[s], p.a_bytes + (p.b_resident ? 0u : p.b_bytes));
+                    tma_load_5d(dst, &tmA, 0, tx * TC_TX - R, ty * TC_TY - R, tz * p.ZT - R, k * (p.KC / 8), &full[s]);
+                    if (!p.b_resident) tma_load_4d(dst + p.a_stride, &tmB, 0, nt * p.NT, k * (p.KC / 8), 0, &full[s]);
+                    if (++s == NS) { s = 0; ph ^= 1u; }
+                }
+            }
+            // every load issued has landed before the CTA ends (the MMA warp waited on each; this
+            // only matters after a wait gave up)
+            for (int q = 0; q < NS; ++q) {
+                int s2 = s - 1 - q;
+                uint32_t ph2 = ph;
+                if (s2 < 0) { s2 += NS; ph2 ^= 1u; }
+                mbar_wait_n(&full[s2], ph2, WAIT_LIMIT / 16);
             }
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    for (int s = 0; s < TC_STAGES - 1; ++s) gather(s);
-    for (int s = 0; s < S; ++s) {
-        // stage s's group is complete once at most TC_STAGES - 2 newer groups are pending
-        asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 2) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // generic writes -> tensor-core reads
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            unsigned char* buf = sm + (s % TC_STAGES) * stBytes;
-            for (int ks = 0; ks < Kc / 16; ++ks)
-                tc_mma(tmem, smem_desc(buf + ks * 2 * lbo, lbo, sbo), smem_desc(buf + aBytes + ks * 2 * lbo, lbo, sbo),
-                       idesc, (s > 0 || ks > 0) ? 1u : 0u);
-            tc_commit(&mbar[s % TC_STAGES]);
-        }
-        // refill the buffer of stage s - 1 with stage s + TC_STAGES - 1 once its MMAs are done
-        const int sn = s + TC_STAGES - 1;
-        if (sn < S && s >= 1) {
-            const int sp = s - 1;
-            if (!mbar_wait(&mbar[sp % TC_STAGES], (uint32_t)((sp / TC_STAGES) & 1))) ok = false;
-        }
-        gather(sn);
-    }
-    // the last commit covers every MMA issued before it
-    if (!mbar_wait(&mbar[(S - 1) % TC_STAGES], (uint32_t)(((S - 1) / TC_STAGES) & 1))) ok = false;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    tc_fence_after();
-    if (!ok) atomicMax(&g_conv_tc_status, 1);
-    for (int cc = 0; cc < NT; cc += 16) {
-        uint32_t r[16];
-        tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc, r);
-        if (vok) {
-            uint32_t pk[8];
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc(p.NT, 128);
+            const uint32_t lboA = p.a_bytes / (p.KC / 8);        // one 8-channel chunk of the halo
+            const uint32_t lboB = (uint32_t)p.NT * 16;
+            if (p.b_resident && ok && !mbar_wait(wbar, 0)) ok = false;
+            int s = 0, ab = 0;
+            uint32_t ph = 0, aph = 0;
+            for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+                if (ok && !mbar_wait(&acc_empty[ab], aph ^ 1u)) ok = false;
+                tc_fence_after();
+                const uint32_t dcol = tmem + (uint32_t)(ab * p.ZT * p.NT);
+                for (int k = 0; k < p.nK; ++k) {
+                    if (ok && !mbar_wait(&full[s], ph)) ok = false;
+                    tc_fence_after();
+                    const uint32_t aaddr = smem_u32(sm + (size_t)s * stage_bytes);
+                    const uint32_t baddr = p.b_resident ? smem_u32(bres) : aaddr + p.a_stride;
+                    const uint64_t a0 = smem_desc(aaddr, lboA, HX * 16);
+                    const uint64_t b0 = smem_desc(baddr, lboB, 128);
+                    for (int zs = 0; zs < p.ZT; ++zs) {
+                        const uint64_t az = a0 + (uint64_t)(zs * HY * HX);      // 16-byte units
+                        for (int kk = 0; kk < p.KC / 16; ++kk) {
+                            const uint64_t ak = az + (uint64_t)(kk * 2 * (lboA >> 4));
+                            const uint64_t bk = b0 + (uint64_t)(kk * 2 * (lboB >> 4));
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float o0 = __uint_as_float(r[2 * q]), o1 = __uint_as_float(r[2 * q + 1]);
-                if (bias) { o0 += bias[co0 + cc + 2 * q]; o1 += bias[co0 + cc + 2 * q + 1]; }
-                if (relu) { o0 = fmaxf(o0, 0.f); o1 = fmaxf(o1, 0.f); }
-                pk[q] = (uint32_t)f2bf_rn(o0) | ((uint32_t)f2bf_rn(o1) << 16);
+                            for (int t = 0; t < TAPS; ++t) {
+                                const int dz = TAPS == 27 ? t / 9 : 0, dy = TAPS == 27 ? (t / 3) % 3 : 0,
+                                          dx = TAPS == 27 ? t % 3 : 0;
+                                const uint64_t at = ak + (uint64_t)((dz * HY + dy) * HX + dx);
+                                const uint64_t bt = bk + (uint64_t)(t * (p.KC / 8) * (lboB >> 4));
+                                tc_mma(dcol + (uint32_t)(zs * p.NT), at, bt, idesc, (k | kk | t) != 0 ? 1u : 0u);
+                            }
+                        }
+                    }
+                    tc_commit(&empty[s]);         // the stage's slot is free once these MMAs are done
+                    if (++s == NS) { s = 0; ph ^= 1u; }
+                }
+                tc_commit(&acc_full[ab]);
+                if (++ab == 2) { ab = 0; aph ^= 1u; }
             }
-            uint4* dst = reinterpret_cast<uint4*>(out + v * Cout + co0 + cc);
-            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    } else {
+        // ---- epilogue: TMEM lanes 32 q ... 32 q + 31, q = warp mod 4; lane m <-> voxel (m % 8, m / 8)
+        const int q = warp & 3;
+        const int m = 32 * q + lane;
+        const int lx = m & 7, ly = m >> 3;
+        int ab = 0;
+        uint32_t aph = 0;
+        for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+            const int nt = (int)(u % p.n_tiles);
+            const int64_t st = u / p.n_tiles;
+            const int tx = (int)(st % p.tiles_x), ty = (int)((st / p.tiles_x) % p.tiles_y);
+            const int tz = (int)(st / ntile_xy);
+            if (ok && !mbar_wait(&acc_full[ab], aph)) ok = false;
+            tc_fence_after();
+            const int x = tx * TC_TX + lx, y = ty * TC_TY + ly;
+            const int n0 = nt * p.NT;
+            for (int zs = 0; zs < p.ZT; ++zs) {
+                const int z = tz * p.ZT + zs;
+                const bool inb = x < p.W && y < p.H && z < p.D;
+                const int64_t o = inb ? (((int64_t)z * p.H + y) * p.W + x) * p.Cout + n0 : 0;
+                for (int c0 = 0; c0 < p.NT; c0 += 16) {
+                    uint32_t r[16];
+                    tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * p.ZT * p.NT + zs * p.NT + c0), r);
+                    if (inb) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float o0 = __uint_as_float(r[2 * i]), o1 = __uint_as_float(r[2 * i + 1]);
+                            if (p.bias) { o0 += p.bias[n0 + c0 + 2 * i]; o1 += p.bias[n0 + c0 + 2 * i + 1]; }
+                            if (p.relu) { o0 = fmaxf(o0, 0.f); o1 = fmaxf(o1, 0.f); }
+                            pk[i] = (uint32_t)f2bf_rn(o0) | ((uint32_t)f2bf_rn(o1) << 16);
+                        }
+                        uint4* d4 = reinterpret_cast<uint4*>(p.out + o + c0);
+                        d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+            if (++ab == 2) { ab = 0; aph ^= 1u; }
         }
     }
+    if (!ok) atomicMax(&g_conv_tc_status, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+    }
 }
 
-// Eligible shapes: Cin and Cout multiples of 16, a channel tile NT = Cout (<= 128) or 128, 16-byte
-// aligned tensors.  Returns cudaErrorNotSupported otherwise (the caller uses the mma.sync kernel).
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 conv_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+int channel_tile(int Cout) {
+    if (Cout <= 64) return Cout;
+    for (int nt : {64, 48, 32, 16})
+        if (Cout % nt == 0) return nt;
+    return 0;
+}
+
+uint32_t tmem_columns(int n) {
+    uint32_t c = 32;
+    while (c < (uint32_t)n) c <<= 1;
+    return c;
+}
+
+}  // namespace
+
+// Eligible shapes: Cin and Cout multiples of 16, 1 or 27 taps, 16-byte aligned tensors.  Returns
+// cudaErrorNotSupported otherwise (the caller then uses the mma.sync kernel).
 cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Cin, const uint16_t* w,
                                  const float* bias, int Cout, int taps, int relu, uint16_t* out, cudaStream_t st) {
-    if (Cin % 16 != 0 || Cout % 16 != 0) return cudaErrorNotSupported;
-    const int NT = Cout <= 128 ? Cout : (Cout % 128 == 0 ? 128 : 0);
-    if (NT == 0) return cudaErrorNotSupported;
+    if (Cin % 16 != 0 || Cout % 16 != 0 || (taps != 27 && taps != 1)) return cudaErrorNotSupported;
     if (((uintptr_t)in | (uintptr_t)w | (uintptr_t)out) & 15) return cudaErrorNotSupported;
-    const int Kc = Cin % 32 == 0 ? 32 : 16;
-    const int ncols = NT <= 32 ? 32 : (NT <= 64 ? 64 : 128);
-    const size_t smem = TC_STAGES * ((size_t)TC_M * Kc * 2 + (size_t)NT * Kc * 2) + 8 * TC_STAGES + 16;
-    cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int NT = channel_tile(Cout);
+    if (NT == 0) return cudaErrorNotSupported;
+    auto enc = conv_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const int R = taps == 27 ? 1 : 0;
+    const int HX = TC_TX + 2 * R, HY = TC_TY + 2 * R;
+    const int sms = device_sms();
+    const int tiles_x = (W + TC_TX - 1) / TC_TX, tiles_y = (H + TC_TY - 1) / TC_TY;
+    const int n_tiles = Cout / NT;
+    const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 5) + 16;
+
+    // z-slices per tile: the largest that keeps at least one unit per SM (two accumulator buffers
+    // of ZT x NT columns in the 512 of tensor memory); then the most channels per stage that let
+    // two stages fit in shared memory.
+    ConvTcArgs a{};
+    int ZT = 8;
+    while (ZT > 1 && (2 * ZT * NT > 512 || (int64_t)((D + ZT - 1) / ZT) * tiles_x * tiles_y * n_tiles < sms)) ZT >>= 1;
+    if (2 * ZT * NT > 512) return cudaErrorNotSupported;
+    int KC = 0;
+    for (;;) {
+        for (int kc = Cin; kc >= 16; kc -= 16) {
+            if (Cin % kc != 0 || kc / 8 > 256) continue;
+            const size_t abytes = (size_t)16 * HX * HY * (ZT + 2 * R) * (kc / 8);
+            const size_t astr = (abytes + 1023) & ~(size_t)1023;
+            const size_t bbytes = (size_t)taps * NT * kc * 2;
+            const bool res = kc == Cin && n_tiles == 1;
+            const size_t need = 2 * (astr + (res ? 0 : bbytes)) + (res ? bbytes : 0) + bar_bytes;
+            if (need <= TC_SMEM_MAX) { KC = kc; break; }
+        }
+        if (KC || ZT == 1) break;
+        ZT >>= 1;
+    }
+    if (KC == 0) return cudaErrorNotSupported;
+    a.D = D; a.H = H; a.W = W; a.Cout = Cout;
+    a.NT = NT; a.ZT = ZT; a.KC = KC; a.nK = Cin / KC;
+    a.tiles_x = tiles_x; a.tiles_y = tiles_y; a.n_tiles = n_tiles;
+    a.units = (int64_t)((D + ZT - 1) / ZT) * tiles_x * tiles_y * n_tiles;
+    a.a_bytes = (uint32_t)(16 * HX * HY * (ZT + 2 * R) * (KC / 8));
+    a.a_stride = (a.a_bytes + 1023u) & ~1023u;
+    a.b_bytes = (uint32_t)(taps * NT * KC * 2);
+    a.b_resident = (KC == Cin && n_tiles == 1) ? 1 : 0;
+    a.tmem_cols = tmem_columns(2 * ZT * NT);
+    a.relu = relu;
+    a.bias = bias;
+    a.out = out;
+    const size_t stage = a.a_stride + (a.b_resident ? 0 : a.b_bytes);
+    int ns = (int)((TC_SMEM_MAX - bar_bytes - (a.b_resident ? a.b_bytes : 0)) / stage);
+    a.nstages = ns < TC_MAX_STAGES ? ns : TC_MAX_STAGES;
+    if (a.nstages < 2) return cudaErrorNotSupported;
+    const size_t smem = (size_t)a.nstages * stage + (a.b_resident ? a.b_bytes : 0) + bar_bytes;
+
+    // input halo: dims (8 channels, x, y, z, channel chunk), box (8, HX, HY, ZT + 2R, KC / 8);
+    // out-of-range voxels read as zero
+    CUtensorMap mA, mB;
+    {
+        cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cin / 8)};
+        cuuint64_t strides[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2, 16};
+        cuuint32_t box[5] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)(ZT + 2 * R), (cuuint32_t)(KC / 8)};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(in), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    // weights w[co][tap][ci]: dims (8 channels, co, channel chunk, tap), box (8, NT, KC / 8, taps)
+    {
+        cuuint64_t dims[4] = {8, (cuuint64_t)Cout, (cuuint64_t)(Cin / 8), (cuuint64_t)taps};
+        cuuint64_t strides[3] = {(cuuint64_t)taps * Cin * 2, 16, (cuuint64_t)Cin * 2};
+        cuuint32_t box[4] = {8, (cuuint32_t)NT, (cuuint32_t)(KC / 8), (cuuint32_t)taps};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(w), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    auto kern = taps == 27 ? conv3d_fwd_tc_kernel<27> : conv3d_fwd_tc_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t nv = (int64_t)D * H * W;
-    dim3 grid((unsigned)((nv + TC_M - 1) / TC_M), (unsigned)(Cout / NT));
-    conv3d_fwd_tc_kernel<<<grid, TC_THREADS, smem, st>>>(in, D, H, W, Cin, w, bias, Cout, NT, ncols, taps, relu, Kc,
-                                                         out);
+    const int64_t grid = a.units < sms ? a.units : sms;
+    kern<<<(unsigned)grid, TC_THREADS, smem, st>>>(mA, mB, a);
     return cudaGetLastError();
 }
 

@@ -70,8 +70,8 @@ def _ck(name, code):
 # ---------------------------------------------------------------- thin wrappers (same names)
 
 def gpair_unet_tensor_path(mode: int = -1) -> int:
-    """1 (default): tcgen05 tensor-core convolutions for Cout >= 64; 2: for every eligible shape;
-    0: mma.sync only; other values query.  Returns the mode in force."""
+    """1 (default): the tcgen05 tensor-core convolution for every eligible shape, mma.sync for the
+    others; 2: tcgen05 only; 0: mma.sync only; other values query.  Returns the mode in force."""
     return int(_unet_lib().gpair_unet_tensor_path(int(mode)))
 
 
