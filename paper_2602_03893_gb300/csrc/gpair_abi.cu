@@ -615,6 +615,9 @@ gpair_status run_adjoint(const GaussDev& g, const ArrDev& a, const float* delta,
 }  // namespace
 
 namespace gp {
+// The calling stream's pooled device scratch, at least `bytes` long (grown on demand).
+gpair_status stream_scratch(cudaStream_t st, size_t bytes, void** buf) { return get_scratch(st, bytes, buf, nullptr); }
+
 // The forward operator run entirely inside caller-provided scratch (`cap` bytes of device memory
 // at `scratch`, plus a device status word): validates, plans within the capacity and launches.
 // Allocates nothing.  Used by the allocation-free entry point.

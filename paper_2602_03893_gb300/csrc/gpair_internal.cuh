@@ -302,6 +302,10 @@ struct KahanF {
 // query fails, so launches stay valid.
 int device_sms();
 
+// Device scratch of the calling stream (one pool per device and stream, shared by every call on
+// that stream, so stream order keeps its users apart), at least `bytes` long.  Host only.
+gpair_status stream_scratch(cudaStream_t st, size_t bytes, void** buf);
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicMax(status, code);
 }

@@ -7,7 +7,8 @@
 // mma.sync.m16n8k16 (bf16 x bf16 -> f32) with fragments gathered straight from the L1/L2-resident
 // input and weights; zero padding is applied at fragment load.  The data gradient is the same
 // kernel run on flipped, channel-transposed weights; the weight gradient is a GEMM over voxels
-// (split-K across CTAs, FP32 atomics into the gradient).
+// (split-K across CTAs, FP32 atomics into the gradient).  These mma.sync kernels serve the shapes
+// the tcgen05 kernels (unet_tc.cu) do not take, and tensor path 0.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -386,6 +387,8 @@ int g_tensor_path = 1;
 namespace gp {
 cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Cin, const uint16_t* w,
                                  const float* bias, int Cout, int taps, int relu, uint16_t* out, cudaStream_t st);
+cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int D, int H, int W, int Cin, int Cout,
+                                   int taps, float* dw, cudaStream_t st);
 int conv_tc_status_and_clear();
 }  // namespace gp
 
@@ -442,8 +445,21 @@ gpair_status gpair_conv3d_wgrad(const gpair_bf16* in, const gpair_bf16* dout, in
     if (Cin % 8 != 0 || Cout % 16 != 0 || Cin > 256) return GPAIR_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t nv = (int64_t)D * H * W;
+    bool done = false;
+    if (g_tensor_path != 0) {
+        const cudaError_t e = gp::launch_conv3d_wgrad_tc(reinterpret_cast<const uint16_t*>(in),
+                                                         reinterpret_cast<const uint16_t*>(dout), D, H, W, Cin, Cout,
+                                                         taps, dw, s);
+        if (e == cudaErrorMemoryAllocation) return GPAIR_ERR_NOMEM;
+        if (e != cudaErrorNotSupported && e != cudaSuccess) return GPAIR_ERR_CUDA;
+        if (e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            if (g_tensor_path == 2) return GPAIR_ERR_UNSUPPORTED;
+        }
+        done = e == cudaSuccess;
+    }
     dim3 grid((unsigned)((nv + WG_CHUNK - 1) / WG_CHUNK), taps, Cout / 16);
-    switch (Cin / 8) {
+    if (!done) switch (Cin / 8) {
 #define GP_WG(N) case N: conv3d_wgrad_kernel<N><<<grid, 128, 0, s>>>(in, dout, D, H, W, Cin, Cout, taps, dw); break;
         GP_WG(1) GP_WG(2) GP_WG(3) GP_WG(4) GP_WG(6) GP_WG(8) GP_WG(12) GP_WG(16) GP_WG(24) GP_WG(32)
 #undef GP_WG

@@ -399,6 +399,234 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Weight gradient: dW[co][t][ci] = sum_v dout[v][co] in[v + off(t)][ci], a GEMM whose rows are
+// (tap, input channel), columns output channels and reduction the voxels.  Both operands are
+// MN-major: a core matrix is 8 voxels (K, consecutive in x) x 8 channels (16 bytes), which is how
+// a TMA box [8-channel chunk][z][y][x][8] of channels-last data lands.  The rows of one MMA
+// (M = 128) are 8 units of (tap, 16 input channels), each unit one TMA box of the input shifted
+// by its tap; K = 16 is two x-rows of 8 voxels; the dout box of the same voxels is the B operand.
+// CTA = (group of 128-row blocks held in tensor memory, range of voxel tiles): it accumulates
+// over its tiles and writes its partial dW; wgrad_reduce_kernel sums the partials in fixed order.
+
+constexpr int WG_THREADS = 128;        // warp 0: TMA, warp 1: MMA; all four drain tensor memory
+constexpr int WG_UNITS = 8;            // (tap, 16-channel) units per 128-row block
+
+struct WgradTcArgs {
+    int Cin, Cout, taps, ZS;
+    int tiles_x, tiles_y, n_tiles;     // voxel tiles of 8 x 16 x ZS
+    int units, blocks;                 // (tap, 16-channel) units = taps Cin / 16; 128-row blocks
+    int G, n_groups, n_splits;         // blocks per group (tensor memory), groups, voxel-tile splits
+    int nstages;
+    uint32_t unit_bytes, b_bytes, stage_bytes, tmem_cols;
+    float* partial;                    // [split][taps * Cin][Cout]
+};
+
+// MN-major A and B (bits 15, 16), FP32 accumulator, BF16 operands.
+__host__ __device__ constexpr uint32_t tc_idesc_mn(int N, int M) { return tc_idesc(N, M) | (1u << 15) | (1u << 16); }
+
+template <int TAPS>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmOut,
+                       const WgradTcArgs p) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int R = TAPS == 27 ? 1 : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NS = p.nstages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)NS * p.stage_bytes);
+    uint64_t* empty = full + TC_MAX_STAGES;
+    uint64_t* done = empty + TC_MAX_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int grp = (int)(blockIdx.x % p.n_groups), split = (int)(blockIdx.x / p.n_groups);
+    const int b0 = grp * p.G, b1 = min(p.blocks, b0 + p.G);
+    const int t0 = (int)((int64_t)split * p.n_tiles / p.n_splits), t1 = (int)((int64_t)(split + 1) * p.n_tiles / p.n_splits);
+    const int cp_per_tap = p.Cin / 16;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(p.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        int s = 0;
+        uint32_t ph = 0;
+        for (int tile = t0; tile < t1; ++tile) {
+            const int tx = tile % p.tiles_x, ty = (tile / p.tiles_x) % p.tiles_y, tz = tile / (p.tiles_x * p.tiles_y);
+            const int x0 = tx * TC_TX, y0 = ty * TC_TY, z0 = tz * p.ZS;
+            for (int b = b0; b < b1; ++b) {
+                if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
+                const uint32_t dst = smem_u32(sm + (size_t)s * p.stage_bytes);
+                const int nu = min(WG_UNITS, p.units - b * WG_UNITS);
+                mbar_arrive_expect_tx(&full[s], (uint32_t)nu * p.unit_bytes + p.b_bytes);
+                for (int u = 0; u < nu; ++u) {
+                    const int U = b * WG_UNITS + u;
+                    const int t = U / cp_per_tap, cp = U - t * cp_per_tap;
+                    const int dz = TAPS == 27 ? t / 9 : 0, dy = TAPS == 27 ? (t / 3) % 3 : 0, dx = TAPS == 27 ? t % 3 : 0;
+                    tma_load_5d(dst + (uint32_t)u * p.unit_bytes, &tmIn, 0, x0 + dx - R, y0 + dy - R, z0 + dz - R, 2 * cp,
+                                &full[s]);
+                }
+                tma_load_5d(dst + WG_UNITS * p.unit_bytes, &tmOut, 0, x0, y0, z0, 0, &full[s]);
+                if (++s == NS) { s = 0; ph ^= 1u; }
+            }
+        }
+        for (int q = 0; q < NS; ++q) {      // every load issued has landed before the CTA ends
+            int s2 = s - 1 - q;
+            uint32_t ph2 = ph;
+            if (s2 < 0) { s2 += NS; ph2 ^= 1u; }
+            mbar_wait_n(&full[s2], ph2, WAIT_LIMIT / 16);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = tc_idesc_mn(p.Cout, 128);
+        const uint32_t csz = p.unit_bytes / 2;             // one 8-channel chunk of a unit's box
+        const int ksteps = TC_TX * TC_TY * p.ZS / 16;
+        int s = 0;
+        uint32_t ph = 0;
+        for (int tile = t0; tile < t1; ++tile) {
+            for (int b = b0; b < b1; ++b) {
+                if (ok && !mbar_wait(&full[s], ph)) ok = false;
+                tc_fence_after();
+                const uint32_t aaddr = smem_u32(sm + (size_t)s * p.stage_bytes);
+                // MN-major, no swizzle: LBO = K-direction core-matrix stride (one x-row of 8 voxels,
+                // 128 bytes), SBO = M/N-direction stride (one 8-channel chunk)
+                const uint64_t a0 = smem_desc(aaddr, 128, csz);
+                const uint64_t bq = smem_desc(aaddr + WG_UNITS * p.unit_bytes, 128, csz);
+                const uint32_t d = tmem + (uint32_t)((b - b0) * p.Cout);
+                for (int kk = 0; kk < ksteps; ++kk)
+                    tc_mma(d, a0 + (uint64_t)(kk * 16), bq + (uint64_t)(kk * 16), idesc,
+                           (tile > t0 || kk > 0) ? 1u : 0u);
+                tc_commit(&empty[s]);
+                if (++s == NS) { s = 0; ph ^= 1u; }
+            }
+        }
+        tc_commit(done);
+    }
+    __syncwarp();
+    // drain: warp w holds TMEM lanes 32w ... 32w + 31, i.e. rows 32w + lane of each block
+    if (t1 > t0) {
+        if (ok && !mbar_wait(done, 0)) ok = false;
+        tc_fence_after();
+        const int rows = p.taps * p.Cin;
+        for (int b = b0; b < b1; ++b) {
+            const int m = b * 128 + 32 * warp + lane;
+            float* dst = p.partial + ((size_t)split * rows + (m < rows ? m : 0)) * p.Cout;
+            for (int c0 = 0; c0 < p.Cout; c0 += 16) {
+                uint32_t r[16];
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((b - b0) * p.Cout + c0), r);
+                if (m < rows) {
+                    float4* d4 = reinterpret_cast<float4*>(dst + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        d4[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                            __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                }
+            }
+        }
+    }
+    if (!ok) atomicMax(&g_conv_tc_status, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols));
+    }
+}
+
+// dw[co][t][ci] += sum over splits (in order) of partial[split][t Cin + ci][co]
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int n_splits, int rows, int Cout,
+                                    float* __restrict__ dw) {
+    const int64_t n = (int64_t)rows * Cout;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(i / rows), m = (int)(i - (int64_t)co * rows);   // dw index co * rows + m
+        float acc = 0.f;
+        for (int s = 0; s < n_splits; ++s) acc += partial[((size_t)s * rows + m) * Cout + co];
+        dw[i] += acc;
+    }
+}
+
+// Eligible: Cin and Cout multiples of 16, Cout <= 256, 1 or 27 taps, 16-byte aligned tensors.
+// The partial sums live in the stream's scratch pool.
+cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int D, int H, int W, int Cin, int Cout,
+                                   int taps, float* dw, cudaStream_t st) {
+    if (Cin % 16 != 0 || Cout % 16 != 0 || Cout > 256 || (taps != 27 && taps != 1)) return cudaErrorNotSupported;
+    if (((uintptr_t)in | (uintptr_t)dout) & 15) return cudaErrorNotSupported;
+    auto enc = conv_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const int sms = device_sms();
+    WgradTcArgs a{};
+    a.Cin = Cin; a.Cout = Cout; a.taps = taps; a.ZS = 1;
+    a.tiles_x = (W + TC_TX - 1) / TC_TX; a.tiles_y = (H + TC_TY - 1) / TC_TY;
+    a.n_tiles = a.tiles_x * a.tiles_y * ((D + a.ZS - 1) / a.ZS);
+    a.units = taps * Cin / 16;
+    a.blocks = (a.units + WG_UNITS - 1) / WG_UNITS;
+    a.G = 512 / Cout < a.blocks ? 512 / Cout : a.blocks;
+    a.n_groups = (a.blocks + a.G - 1) / a.G;
+    a.G = (a.blocks + a.n_groups - 1) / a.n_groups;        // even groups
+    int ns = sms / a.n_groups;
+    if (ns < 1) ns = 1;
+    if (ns > a.n_tiles) ns = a.n_tiles;
+    a.n_splits = ns;
+    a.unit_bytes = (uint32_t)(2 * 16 * TC_TX * TC_TY * a.ZS);     // 2 chunks x 8 channels x voxels x 2 B
+    a.b_bytes = (uint32_t)(TC_TX * TC_TY * a.ZS * Cout * 2);
+    a.stage_bytes = (WG_UNITS * a.unit_bytes + a.b_bytes + 1023u) & ~1023u;
+    a.tmem_cols = tmem_columns(a.G * Cout);
+    const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 1) + 16;
+    int nst = (int)((TC_SMEM_MAX - bar_bytes) / a.stage_bytes);
+    a.nstages = nst < TC_MAX_STAGES ? nst : TC_MAX_STAGES;
+    if (a.nstages < 2 || a.tmem_cols > 512) return cudaErrorNotSupported;
+    const size_t smem = (size_t)a.nstages * a.stage_bytes + bar_bytes;
+    const int rows = taps * Cin;
+    void* scratch = nullptr;
+    if (stream_scratch(st, (size_t)a.n_splits * rows * Cout * sizeof(float), &scratch) != GPAIR_OK)
+        return cudaErrorMemoryAllocation;
+    a.partial = static_cast<float*>(scratch);
+
+    CUtensorMap mI, mO;
+    const int R = taps == 27 ? 1 : 0;
+    (void)R;
+    {
+        cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cin / 8)};
+        cuuint64_t strides[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2, 16};
+        cuuint32_t box[5] = {8, TC_TX, TC_TY, (cuuint32_t)a.ZS, 2};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&mI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(in), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    {
+        cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cout / 8)};
+        cuuint64_t strides[4] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2, 16};
+        cuuint32_t box[5] = {8, TC_TX, TC_TY, (cuuint32_t)a.ZS, (cuuint32_t)(Cout / 8)};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&mO, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(dout), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    auto kern = taps == 27 ? conv3d_wgrad_tc_kernel<27> : conv3d_wgrad_tc_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(a.n_groups * a.n_splits), WG_THREADS, smem, st>>>(mI, mO, a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t n = (int64_t)rows * Cout;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    wgrad_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.partial, a.n_splits, rows, Cout, dw);
+    return cudaGetLastError();
+}
+
 int conv_tc_status_and_clear() {
     int h = 0, z = 0;
     cudaMemcpyFromSymbol(&h, g_conv_tc_status, sizeof(int));
