@@ -17,6 +17,7 @@
 
 namespace gp {
 int device_sms();   // SMs of the current device (step.cu)
+gpair_status stream_scratch(cudaStream_t st, size_t bytes, void** buf);   // the stream's scratch pool (gpair_abi.cu)
 }
 
 namespace {
@@ -216,16 +217,42 @@ conv3d_wgrad_kernel(const bf16_t* __restrict__ in, const bf16_t* __restrict__ do
     }
 }
 
-// db[co] += sum_v dout[v][co]
-__global__ void bias_grad_kernel(const bf16_t* __restrict__ dout, int64_t nv, int Cout, float* __restrict__ db) {
-    extern __shared__ float sacc[];
-    for (int q = threadIdx.x; q < Cout; q += blockDim.x) sacc[q] = 0.f;
+// db[co] += sum_v dout[v][co], in two deterministic passes.  Pass 1: block (Cout / 8) x rows
+// threads; thread (c, r) sums channels 8c ... 8c + 7 of the voxels r, r + rows, ... of its block's
+// range (16-byte loads, consecutive threads on consecutive chunks), then the block sums its rows
+// in shared memory in fixed order and writes part[block][Cout].
+__global__ void bias_grad_part_kernel(const bf16_t* __restrict__ dout, int64_t nv, int Cout, int64_t per_block,
+                                      float* __restrict__ part) {
+    extern __shared__ float sred[];                 // [rows][Cout]
+    const int nc = Cout / 8, c = threadIdx.x, r = threadIdx.y, rows = blockDim.y;
+    const int64_t v0 = blockIdx.x * per_block, v1 = min(nv, v0 + per_block);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t v = v0 + r; v < v1; v += rows) {
+        const uint4 q = *reinterpret_cast<const uint4*>(dout + v * Cout + 8 * c);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[2 * i] += __uint_as_float(w[i] << 16);
+            acc[2 * i + 1] += __uint_as_float(w[i] & 0xFFFF0000u);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sred[r * Cout + 8 * c + i] = acc[i];
     __syncthreads();
-    const int64_t n = nv * Cout;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&sacc[i % Cout], bf2f(dout[i]));
-    __syncthreads();
-    for (int q = threadIdx.x; q < Cout; q += blockDim.x) atomicAdd(&db[q], sacc[q]);
+    for (int q = r * nc + c; q < Cout; q += rows * nc) {
+        float s = 0.f;
+        for (int k = 0; k < rows; ++k) s += sred[k * Cout + q];
+        part[(int64_t)blockIdx.x * Cout + q] = s;
+    }
+}
+
+// Pass 2: db[co] += sum over blocks (in order) of part[block][co].
+__global__ void bias_grad_sum_kernel(const float* __restrict__ part, int nblocks, int Cout, float* __restrict__ db) {
+    for (int co = threadIdx.x; co < Cout; co += blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * Cout + co];
+        db[co] += s;
+    }
 }
 
 __global__ void relu_bwd_kernel(const bf16_t* __restrict__ act, bf16_t* __restrict__ g, int64_t n) {
@@ -466,7 +493,19 @@ gpair_status gpair_conv3d_wgrad(const gpair_bf16* in, const gpair_bf16* dout, in
         default: return GPAIR_ERR_UNSUPPORTED;
     }
     if (cudaGetLastError() != cudaSuccess) return GPAIR_ERR_CUDA;
-    if (db) bias_grad_kernel<<<blocks_for(nv * Cout), 256, Cout * sizeof(float), s>>>(dout, nv, Cout, db);
+    if (db) {
+        if (((uintptr_t)dout & 15) != 0 || Cout % 8 != 0 || Cout > 256) return GPAIR_ERR_UNSUPPORTED;
+        const int nc = Cout / 8, rows = 256 / nc;
+        int64_t nb = (int64_t)gp::device_sms() * 2;
+        const int64_t per_block = (nv + nb - 1) / nb;
+        nb = (nv + per_block - 1) / per_block;
+        void* part = nullptr;
+        if (gp::stream_scratch(s, (size_t)nb * Cout * sizeof(float), &part) != GPAIR_OK) return GPAIR_ERR_NOMEM;
+        bias_grad_part_kernel<<<(unsigned)nb, dim3(nc, rows), (size_t)rows * Cout * sizeof(float), s>>>(
+            dout, nv, Cout, per_block, static_cast<float*>(part));
+        if (cudaGetLastError() != cudaSuccess) return GPAIR_ERR_CUDA;
+        bias_grad_sum_kernel<<<1, 256, 0, s>>>(static_cast<const float*>(part), (int)nb, Cout, db);
+    }
     return st(cudaGetLastError());
 }
 

@@ -402,10 +402,11 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
 // ------------------------------------------------------------------------------------------
 // Weight gradient: dW[co][t][ci] = sum_v dout[v][co] in[v + off(t)][ci], a GEMM whose rows are
 // (tap, input channel), columns output channels and reduction the voxels.  Both operands are
-// MN-major: a core matrix is 8 voxels (K, consecutive in x) x 8 channels (16 bytes), which is how
-// a TMA box [8-channel chunk][z][y][x][8] of channels-last data lands.  The rows of one MMA
-// (M = 128) are 8 units of (tap, 16 input channels), each unit one TMA box of the input shifted
-// by its tap; K = 16 is two x-rows of 8 voxels; the dout box of the same voxels is the B operand.
+// MN-major with the 32-byte swizzle: a voxel's 16 channels are one 32-byte row, 8 voxels
+// consecutive in x one swizzle atom, which is how a TMA box [z][y][x][16 channels] with
+// SWIZZLE_32B lands.  The rows of one MMA (M = 128) are 8 units of (tap, 16 input channels), each
+// unit one TMA box of the input shifted by its tap; K = 16 is two x-rows of 8 voxels; the dout
+// boxes of the same voxels (16 channels each) are the B operand.
 // CTA = (group of 128-row blocks held in tensor memory, range of voxel tiles): it accumulates
 // over its tiles and writes its partial dW; wgrad_reduce_kernel sums the partials in fixed order.
 
@@ -423,6 +424,12 @@ struct WgradTcArgs {
 };
 
 // MN-major A and B (bits 15, 16), FP32 accumulator, BF16 operands.
+// Shared-memory descriptor of an MN-major operand with the 32-byte swizzle (layout type 6 at bits
+// 61-63): LBO = stride between 16-element (32-byte) atoms along M/N, SBO = stride between groups
+// of 8 rows along K.
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    return smem_desc(saddr, lbo_bytes, sbo_bytes) | ((uint64_t)6 << 61);
+}
 __host__ __device__ constexpr uint32_t tc_idesc_mn(int N, int M) { return tc_idesc(N, M) | (1u << 15) | (1u << 16); }
 
 template <int TAPS>
@@ -458,37 +465,43 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
     const uint32_t tmem = *tslot;
     bool ok = true;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0) {
+        // lane 0 claims the slot and posts the byte count; lanes 0 ... 8 then issue one box each
+        // (a box's issue has a fixed cost, so nine lanes keep nine in flight)
         int s = 0;
         uint32_t ph = 0;
         for (int tile = t0; tile < t1; ++tile) {
             const int tx = tile % p.tiles_x, ty = (tile / p.tiles_x) % p.tiles_y, tz = tile / (p.tiles_x * p.tiles_y);
             const int x0 = tx * TC_TX, y0 = ty * TC_TY, z0 = tz * p.ZS;
             for (int b = b0; b < b1; ++b) {
-                if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
                 const uint32_t dst = smem_u32(sm + (size_t)s * p.stage_bytes);
                 const int nu = min(WG_UNITS, p.units - b * WG_UNITS);
-                mbar_arrive_expect_tx(&full[s], (uint32_t)nu * p.unit_bytes + p.b_bytes);
-                for (int u = 0; u < nu; ++u) {
-                    const int U = b * WG_UNITS + u;
+                if (lane == 0) {
+                    if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)nu * p.unit_bytes + p.b_bytes);
+                }
+                __syncwarp();
+                if (lane < nu) {
+                    const int U = b * WG_UNITS + lane;
                     const int t = U / cp_per_tap, cp = U - t * cp_per_tap;
                     const int dz = TAPS == 27 ? t / 9 : 0, dy = TAPS == 27 ? (t / 3) % 3 : 0, dx = TAPS == 27 ? t % 3 : 0;
-                    tma_load_5d(dst + (uint32_t)u * p.unit_bytes, &tmIn, 0, x0 + dx - R, y0 + dy - R, z0 + dz - R, 2 * cp,
+                    tma_load_5d(dst + (uint32_t)lane * p.unit_bytes, &tmIn, 0, x0 + dx - R, y0 + dy - R, z0 + dz - R, cp,
                                 &full[s]);
+                } else if (lane == WG_UNITS) {
+                    tma_load_5d(dst + WG_UNITS * p.unit_bytes, &tmOut, 0, x0, y0, z0, 0, &full[s]);
                 }
-                tma_load_5d(dst + WG_UNITS * p.unit_bytes, &tmOut, 0, x0, y0, z0, 0, &full[s]);
                 if (++s == NS) { s = 0; ph ^= 1u; }
             }
         }
-        for (int q = 0; q < NS; ++q) {      // every load issued has landed before the CTA ends
-            int s2 = s - 1 - q;
-            uint32_t ph2 = ph;
-            if (s2 < 0) { s2 += NS; ph2 ^= 1u; }
-            mbar_wait_n(&full[s2], ph2, WAIT_LIMIT / 16);
-        }
+        if (lane == 0)
+            for (int q = 0; q < NS; ++q) {      // every load issued has landed before the CTA ends
+                int s2 = s - 1 - q;
+                uint32_t ph2 = ph;
+                if (s2 < 0) { s2 += NS; ph2 ^= 1u; }
+                mbar_wait_n(&full[s2], ph2, WAIT_LIMIT / 16);
+            }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = tc_idesc_mn(p.Cout, 128);
-        const uint32_t csz = p.unit_bytes / 2;             // one 8-channel chunk of a unit's box
         const int ksteps = TC_TX * TC_TY * p.ZS / 16;
         int s = 0;
         uint32_t ph = 0;
@@ -497,13 +510,13 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
                 if (ok && !mbar_wait(&full[s], ph)) ok = false;
                 tc_fence_after();
                 const uint32_t aaddr = smem_u32(sm + (size_t)s * p.stage_bytes);
-                // MN-major, no swizzle: LBO = K-direction core-matrix stride (one x-row of 8 voxels,
-                // 128 bytes), SBO = M/N-direction stride (one 8-channel chunk)
-                const uint64_t a0 = smem_desc(aaddr, 128, csz);
-                const uint64_t bq = smem_desc(aaddr + WG_UNITS * p.unit_bytes, 128, csz);
+                // atoms of 16 channels one box (a unit, or 16 output channels) apart; 8-voxel row
+                // groups 256 bytes apart; K = 16 voxels is 512 bytes, a whole number of swizzle repeats
+                const uint64_t a0 = smem_desc_sw32(aaddr, p.unit_bytes, 256);
+                const uint64_t bq = smem_desc_sw32(aaddr + WG_UNITS * p.unit_bytes, p.unit_bytes, 256);
                 const uint32_t d = tmem + (uint32_t)((b - b0) * p.Cout);
                 for (int kk = 0; kk < ksteps; ++kk)
-                    tc_mma(d, a0 + (uint64_t)(kk * 16), bq + (uint64_t)(kk * 16), idesc,
+                    tc_mma(d, a0 + (uint64_t)(kk * 32), bq + (uint64_t)(kk * 32), idesc,
                            (tile > t0 || kk > 0) ? 1u : 0u);
                 tc_commit(&empty[s]);
                 if (++s == NS) { s = 0; ph ^= 1u; }
@@ -565,7 +578,13 @@ cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int
     if (!enc) return cudaErrorNotSupported;
     const int sms = device_sms();
     WgradTcArgs a{};
-    a.Cin = Cin; a.Cout = Cout; a.taps = taps; a.ZS = 1;
+    const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 1) + 16;
+    a.Cin = Cin; a.Cout = Cout; a.taps = taps;
+    // the deepest tile (z-slices) for which two stages fit: fewer, larger boxes
+    a.ZS = 2;
+    while (a.ZS > 1 && 2 * ((size_t)WG_UNITS * 16 * 2 * TC_TX * TC_TY * a.ZS + (size_t)TC_TX * TC_TY * a.ZS * Cout * 2 +
+                            1023) + bar_bytes > TC_SMEM_MAX)
+        --a.ZS;
     a.tiles_x = (W + TC_TX - 1) / TC_TX; a.tiles_y = (H + TC_TY - 1) / TC_TY;
     a.n_tiles = a.tiles_x * a.tiles_y * ((D + a.ZS - 1) / a.ZS);
     a.units = taps * Cin / 16;
@@ -577,11 +596,10 @@ cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int
     if (ns < 1) ns = 1;
     if (ns > a.n_tiles) ns = a.n_tiles;
     a.n_splits = ns;
-    a.unit_bytes = (uint32_t)(2 * 16 * TC_TX * TC_TY * a.ZS);     // 2 chunks x 8 channels x voxels x 2 B
+    a.unit_bytes = (uint32_t)(16 * 2 * TC_TX * TC_TY * a.ZS);     // 16 channels x voxels x 2 B
     a.b_bytes = (uint32_t)(TC_TX * TC_TY * a.ZS * Cout * 2);
     a.stage_bytes = (WG_UNITS * a.unit_bytes + a.b_bytes + 1023u) & ~1023u;
     a.tmem_cols = tmem_columns(a.G * Cout);
-    const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 1) + 16;
     int nst = (int)((TC_SMEM_MAX - bar_bytes) / a.stage_bytes);
     a.nstages = nst < TC_MAX_STAGES ? nst : TC_MAX_STAGES;
     if (a.nstages < 2 || a.tmem_cols > 512) return cudaErrorNotSupported;
@@ -595,23 +613,25 @@ cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int
     CUtensorMap mI, mO;
     const int R = taps == 27 ? 1 : 0;
     (void)R;
+    // input and dout: dims (16 channels, x, y, z, 16-channel group), boxes of 16 channels x 8 x 16 x
+    // ZS voxels (the input: one group per load; dout: all groups), 32-byte swizzle
     {
-        cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cin / 8)};
-        cuuint64_t strides[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2, 16};
-        cuuint32_t box[5] = {8, TC_TX, TC_TY, (cuuint32_t)a.ZS, 2};
+        cuuint64_t dims[5] = {16, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cin / 16)};
+        cuuint64_t strides[4] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2, 32};
+        cuuint32_t box[5] = {16, TC_TX, TC_TY, (cuuint32_t)a.ZS, 1};
         cuuint32_t es[5] = {1, 1, 1, 1, 1};
         if (enc(&mI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(in), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorNotSupported;
     }
     {
-        cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cout / 8)};
-        cuuint64_t strides[4] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2, 16};
-        cuuint32_t box[5] = {8, TC_TX, TC_TY, (cuuint32_t)a.ZS, (cuuint32_t)(Cout / 8)};
+        cuuint64_t dims[5] = {16, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)(Cout / 16)};
+        cuuint64_t strides[4] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2, 32};
+        cuuint32_t box[5] = {16, TC_TX, TC_TY, (cuuint32_t)a.ZS, (cuuint32_t)(Cout / 16)};
         cuuint32_t es[5] = {1, 1, 1, 1, 1};
         if (enc(&mO, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(dout), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorNotSupported;
     }

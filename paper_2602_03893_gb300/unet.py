@@ -366,26 +366,34 @@ class UNet3D:
         self.t = sd["t"]
 
 
-def conv_bench(dims, cin, cout, modes=(1, 2, 0), reps=20, seed=0):
-    """Time gpair_conv3d_fwd (3 x 3 x 3 taps, ReLU) on random BF16 data for each convolution path
-    mode (see gpair_unet_tensor_path).  Returns {mode: (ms, TFLOP/s)}."""
+def conv_bench(dims, cin, cout, modes=(1, 2, 0), reps=20, seed=0, which="fwd"):
+    """Time one convolution pass (3 x 3 x 3 taps) on random BF16 data for each convolution path
+    mode (see gpair_unet_tensor_path): which = "fwd" (with ReLU), "dgrad" or "wgrad" (weight
+    gradient only).  Returns {mode: (ms, TFLOP/s)}."""
     D, H, W = dims
     n = D * H * W
     g = torch.Generator(device="cuda").manual_seed(seed)
     x = torch.randn(n, cin, device="cuda", generator=g).to(torch.bfloat16)
     w = (0.1 * torch.randn(cout, 27, cin, device="cuda", generator=g)).to(torch.bfloat16)
     y = torch.empty(n, cout, device="cuda", dtype=torch.bfloat16)
+    gy = torch.randn(n, cout, device="cuda", generator=g).to(torch.bfloat16)
+    gx = torch.empty(n, cin, device="cuda", dtype=torch.bfloat16)
+    wt = torch.empty(cout * 27 * cin, device="cuda", dtype=torch.bfloat16)
+    dw = torch.zeros(cout, 27, cin, device="cuda")
+    run = {"fwd": lambda: gpair_conv3d_fwd(x, dims, cin, w, None, cout, 27, True, y),
+           "dgrad": lambda: gpair_conv3d_dgrad(gy, dims, cout, w, cin, 27, wt, gx),
+           "wgrad": lambda: gpair_conv3d_wgrad(x, gy, dims, cin, cout, 27, dw, None)}[which]
     prev = gpair_unet_tensor_path(-1)
     out = {}
     try:
         for mode in modes:
             gpair_unet_tensor_path(mode)
-            gpair_conv3d_fwd(x, dims, cin, w, None, cout, 27, True, y)
+            run()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
-                gpair_conv3d_fwd(x, dims, cin, w, None, cout, 27, True, y)
+                run()
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
@@ -403,7 +411,8 @@ if __name__ == "__main__":
     ap.add_argument("--conv-bench", nargs=5, type=int, metavar=("D", "H", "W", "CIN", "COUT"), required=True)
     ap.add_argument("--modes", type=int, nargs="+", default=[1, 2, 0])
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--pass", dest="which", choices=["fwd", "dgrad", "wgrad"], default="fwd")
     a = ap.parse_args()
     D, H, W, cin, cout = a.conv_bench
-    res = conv_bench((D, H, W), cin, cout, tuple(a.modes), a.reps)
+    res = conv_bench((D, H, W), cin, cout, tuple(a.modes), a.reps, which=a.which)
     print(json.dumps({f"mode{m}": {"ms": v[0], "TFLOP/s": v[1]} for m, v in res.items()}))
