@@ -246,13 +246,15 @@ __global__ void bias_grad_part_kernel(const bf16_t* __restrict__ dout, int64_t n
     }
 }
 
-// Pass 2: db[co] += sum over blocks (in order) of part[block][co].
+// Pass 2: db[co] += sum over blocks of part[block][co]; one warp per channel, lane l sums blocks
+// l, l + 32, ... and a fixed shuffle tree adds the lanes (the same order on every run).
 __global__ void bias_grad_sum_kernel(const float* __restrict__ part, int nblocks, int Cout, float* __restrict__ db) {
-    for (int co = threadIdx.x; co < Cout; co += blockDim.x) {
-        float s = 0.f;
-        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * Cout + co];
-        db[co] += s;
-    }
+    const int co = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (co >= Cout) return;
+    float s = 0.f;
+    for (int b = lane; b < nblocks; b += 32) s += part[(int64_t)b * Cout + co];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) db[co] += s;
 }
 
 __global__ void relu_bwd_kernel(const bf16_t* __restrict__ act, bf16_t* __restrict__ g, int64_t n) {
@@ -504,7 +506,7 @@ gpair_status gpair_conv3d_wgrad(const gpair_bf16* in, const gpair_bf16* dout, in
         bias_grad_part_kernel<<<(unsigned)nb, dim3(nc, rows), (size_t)rows * Cout * sizeof(float), s>>>(
             dout, nv, Cout, per_block, static_cast<float*>(part));
         if (cudaGetLastError() != cudaSuccess) return GPAIR_ERR_CUDA;
-        bias_grad_sum_kernel<<<1, 256, 0, s>>>(static_cast<const float*>(part), (int)nb, Cout, db);
+        bias_grad_sum_kernel<<<(Cout + 7) / 8, 256, 0, s>>>(static_cast<const float*>(part), (int)nb, Cout, db);
     }
     return st(cudaGetLastError());
 }

@@ -404,9 +404,12 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
 // (tap, input channel), columns output channels and reduction the voxels.  Both operands are
 // MN-major with the 32-byte swizzle: a voxel's 16 channels are one 32-byte row, 8 voxels
 // consecutive in x one swizzle atom, which is how a TMA box [z][y][x][16 channels] with
-// SWIZZLE_32B lands.  The rows of one MMA (M = 128) are 8 units of (tap, 16 input channels), each
-// unit one TMA box of the input shifted by its tap; K = 16 is two x-rows of 8 voxels; the dout
-// boxes of the same voxels (16 channels each) are the B operand.
+// SWIZZLE_32B lands.  The rows of one MMA (M = 128) are 8 units of 16 input channels, each unit one
+// TMA box of the input shifted by its tap; K = 16 is two x-rows of 8 voxels.  The columns are the
+// output channels of NX = 3 dout boxes shifted by 1 - dx along x (or of one unshifted box, NX = 1,
+// when 3 Cout > 256): with the reduction index u = v + dx - 1, the tap (dz, dy, dx) term is
+// in[u + (0, dy - 1, dz - 1)] dout[u - dx + 1], so a unit is a (dz, dy) shift of the input and the
+// three x-taps share it.  The terms left out at the volume's x faces multiply zero padding.
 // CTA = (group of 128-row blocks held in tensor memory, range of voxel tiles): it accumulates
 // over its tiles and writes its partial dW; wgrad_reduce_kernel sums the partials in fixed order.
 
@@ -416,10 +419,11 @@ constexpr int WG_UNITS = 8;            // (tap, 16-channel) units per 128-row bl
 struct WgradTcArgs {
     int Cin, Cout, taps, ZS;
     int tiles_x, tiles_y, n_tiles;     // voxel tiles of 8 x 16 x ZS
-    int units, blocks;                 // (tap, 16-channel) units = taps Cin / 16; 128-row blocks
+    int NX, N;                         // x-taps carried in the columns (3 or 1); columns = NX Cout
+    int units, blocks;                 // (tap group, 16-channel) units = taps / NX Cin / 16; 128-row blocks
     int G, n_groups, n_splits;         // blocks per group (tensor memory), groups, voxel-tile splits
     int nstages;
-    uint32_t unit_bytes, b_bytes, stage_bytes, tmem_cols;
+    uint32_t unit_bytes, b_bytes, stage_bytes, tmem_cols;    // b_bytes: one dout box
     float* partial;                    // [split][taps * Cin][Cout]
 };
 
@@ -478,17 +482,23 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
                 const int nu = min(WG_UNITS, p.units - b * WG_UNITS);
                 if (lane == 0) {
                     if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
-                    mbar_arrive_expect_tx(&full[s], (uint32_t)nu * p.unit_bytes + p.b_bytes);
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)nu * p.unit_bytes + (uint32_t)p.NX * p.b_bytes);
                 }
                 __syncwarp();
                 if (lane < nu) {
                     const int U = b * WG_UNITS + lane;
-                    const int t = U / cp_per_tap, cp = U - t * cp_per_tap;
-                    const int dz = TAPS == 27 ? t / 9 : 0, dy = TAPS == 27 ? (t / 3) % 3 : 0, dx = TAPS == 27 ? t % 3 : 0;
+                    const int g = U / cp_per_tap, cp = U - g * cp_per_tap;
+                    int dz = 0, dy = 0, dx = R;        // NX = 3: unit g = 3 dz + dy, the x shift is dout's
+                    if (TAPS == 27) {
+                        if (p.NX == 3) { dz = g / 3; dy = g % 3; }
+                        else { dz = g / 9; dy = (g / 3) % 3; dx = g % 3; }
+                    }
                     tma_load_5d(dst + (uint32_t)lane * p.unit_bytes, &tmIn, 0, x0 + dx - R, y0 + dy - R, z0 + dz - R, cp,
                                 &full[s]);
-                } else if (lane == WG_UNITS) {
-                    tma_load_5d(dst + WG_UNITS * p.unit_bytes, &tmOut, 0, x0, y0, z0, 0, &full[s]);
+                } else if (lane >= WG_UNITS && lane < WG_UNITS + p.NX) {
+                    const int j = lane - WG_UNITS;      // dout box of x-tap j: dout[u - j + 1]
+                    tma_load_5d(dst + WG_UNITS * p.unit_bytes + (uint32_t)j * p.b_bytes, &tmOut, 0,
+                                x0 + (p.NX == 3 ? 1 - j : 0), y0, z0, 0, &full[s]);
                 }
                 if (++s == NS) { s = 0; ph ^= 1u; }
             }
@@ -501,7 +511,7 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
                 mbar_wait_n(&full[s2], ph2, WAIT_LIMIT / 16);
             }
     } else if (warp == 1 && lane == 0) {
-        const uint32_t idesc = tc_idesc_mn(p.Cout, 128);
+        const uint32_t idesc = tc_idesc_mn(p.N, 128);
         const int ksteps = TC_TX * TC_TY * p.ZS / 16;
         int s = 0;
         uint32_t ph = 0;
@@ -514,7 +524,7 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
                 // groups 256 bytes apart; K = 16 voxels is 512 bytes, a whole number of swizzle repeats
                 const uint64_t a0 = smem_desc_sw32(aaddr, p.unit_bytes, 256);
                 const uint64_t bq = smem_desc_sw32(aaddr + WG_UNITS * p.unit_bytes, p.unit_bytes, 256);
-                const uint32_t d = tmem + (uint32_t)((b - b0) * p.Cout);
+                const uint32_t d = tmem + (uint32_t)((b - b0) * p.N);
                 for (int kk = 0; kk < ksteps; ++kk)
                     tc_mma(d, a0 + (uint64_t)(kk * 32), bq + (uint64_t)(kk * 32), idesc,
                            (tile > t0 || kk > 0) ? 1u : 0u);
@@ -531,17 +541,25 @@ conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmIn, const __grid_co
         tc_fence_after();
         const int rows = p.taps * p.Cin;
         for (int b = b0; b < b1; ++b) {
-            const int m = b * 128 + 32 * warp + lane;
-            float* dst = p.partial + ((size_t)split * rows + (m < rows ? m : 0)) * p.Cout;
-            for (int c0 = 0; c0 < p.Cout; c0 += 16) {
-                uint32_t r[16];
-                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((b - b0) * p.Cout + c0), r);
-                if (m < rows) {
-                    float4* d4 = reinterpret_cast<float4*>(dst + c0);
+            // row 32 warp + lane of block b: unit U, input channel 16 cp + ci_in; column j Cout + co:
+            // tap (dz, dy, j) (NX = 3) or the unit's own tap (NX = 1)
+            const int mi = 32 * warp + lane;
+            const int U = b * WG_UNITS + mi / 16;
+            const bool valid = U < p.units;
+            const int g = U / cp_per_tap, ci = (U - g * cp_per_tap) * 16 + (mi & 15);
+            for (int j = 0; j < p.NX; ++j) {
+                const int t = p.NX == 3 ? (g / 3) * 9 + (g % 3) * 3 + j : g;
+                float* dst = p.partial + ((size_t)split * rows + (valid ? (size_t)t * p.Cin + ci : 0)) * p.Cout;
+                for (int c0 = 0; c0 < p.Cout; c0 += 16) {
+                    uint32_t r[16];
+                    tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((b - b0) * p.N + j * p.Cout + c0), r);
+                    if (valid) {
+                        float4* d4 = reinterpret_cast<float4*>(dst + c0);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        d4[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
-                                            __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                        for (int i = 0; i < 4; ++i)
+                            d4[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                                __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                    }
                 }
             }
         }
@@ -562,8 +580,18 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int n_spl
     const int64_t n = (int64_t)rows * Cout;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int co = (int)(i / rows), m = (int)(i - (int64_t)co * rows);   // dw index co * rows + m
+        const float* src = partial + (size_t)m * Cout + co;
+        const size_t step = (size_t)rows * Cout;
         float acc = 0.f;
-        for (int s = 0; s < n_splits; ++s) acc += partial[((size_t)s * rows + m) * Cout + co];
+        int s = 0;
+        for (; s + 8 <= n_splits; s += 8) {      // eight loads in flight, added in split order
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = src[(size_t)(s + q) * step];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc += v[q];
+        }
+        for (; s < n_splits; ++s) acc += src[(size_t)s * step];
         dw[i] += acc;
     }
 }
@@ -580,16 +608,18 @@ cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int
     WgradTcArgs a{};
     const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 1) + 16;
     a.Cin = Cin; a.Cout = Cout; a.taps = taps;
+    a.NX = (taps == 27 && 3 * Cout <= 256) ? 3 : 1;
+    a.N = a.NX * Cout;
     // the deepest tile (z-slices) for which two stages fit: fewer, larger boxes
     a.ZS = 2;
-    while (a.ZS > 1 && 2 * ((size_t)WG_UNITS * 16 * 2 * TC_TX * TC_TY * a.ZS + (size_t)TC_TX * TC_TY * a.ZS * Cout * 2 +
-                            1023) + bar_bytes > TC_SMEM_MAX)
+    while (a.ZS > 1 && 2 * ((size_t)WG_UNITS * 16 * 2 * TC_TX * TC_TY * a.ZS +
+                            (size_t)a.NX * TC_TX * TC_TY * a.ZS * Cout * 2 + 1023) + bar_bytes > TC_SMEM_MAX)
         --a.ZS;
     a.tiles_x = (W + TC_TX - 1) / TC_TX; a.tiles_y = (H + TC_TY - 1) / TC_TY;
     a.n_tiles = a.tiles_x * a.tiles_y * ((D + a.ZS - 1) / a.ZS);
-    a.units = taps * Cin / 16;
+    a.units = taps / a.NX * Cin / 16;
     a.blocks = (a.units + WG_UNITS - 1) / WG_UNITS;
-    a.G = 512 / Cout < a.blocks ? 512 / Cout : a.blocks;
+    a.G = 512 / a.N < a.blocks ? 512 / a.N : a.blocks;
     a.n_groups = (a.blocks + a.G - 1) / a.G;
     a.G = (a.blocks + a.n_groups - 1) / a.n_groups;        // even groups
     int ns = sms / a.n_groups;
@@ -598,8 +628,8 @@ cudaError_t launch_conv3d_wgrad_tc(const uint16_t* in, const uint16_t* dout, int
     a.n_splits = ns;
     a.unit_bytes = (uint32_t)(16 * 2 * TC_TX * TC_TY * a.ZS);     // 16 channels x voxels x 2 B
     a.b_bytes = (uint32_t)(TC_TX * TC_TY * a.ZS * Cout * 2);
-    a.stage_bytes = (WG_UNITS * a.unit_bytes + a.b_bytes + 1023u) & ~1023u;
-    a.tmem_cols = tmem_columns(a.G * Cout);
+    a.stage_bytes = (WG_UNITS * a.unit_bytes + (uint32_t)a.NX * a.b_bytes + 1023u) & ~1023u;
+    a.tmem_cols = tmem_columns(a.G * a.N);
     int nst = (int)((TC_SMEM_MAX - bar_bytes) / a.stage_bytes);
     a.nstages = nst < TC_MAX_STAGES ? nst : TC_MAX_STAGES;
     if (a.nstages < 2 || a.tmem_cols > 512) return cudaErrorNotSupported;
