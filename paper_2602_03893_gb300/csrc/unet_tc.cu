@@ -1,16 +1,23 @@
 // unet_tc.cu -- the U-Net's 3-D convolution as an implicit GEMM on the 5th-generation tensor
 // cores (tcgen05.mma kind::f16: BF16 operands, FP32 accumulators in tensor memory), fed by TMA.
 //
-// Tile: 8 (x) x 16 (y) x ZT (z) output voxels and NT output channels.  One MMA takes the 128
-// voxels of one z-slice of the tile (8 x 16) as its rows, the NT channels as its columns and 16
-// input channels of one tap as its K.  The CTA stages the tile's input halo (for a 3 x 3 x 3
-// stencil 10 x 18 x (ZT + 2) voxels, KC channels) with one TMA load in the layout
-// [8-channel chunk][z][y][x][8 channels]: the 8 rows of a core matrix (8 voxels consecutive in x,
-// 16 bytes each) are contiguous, so the operand of tap (dz, dy, dx) and slice zs is the same
-// K-major layout starting ((zs + dz) 18 + dy) 10 + dx rows further in.  Shifting the descriptor
-// replaces the im2col copy; the zero padding is the TMA's out-of-range fill.  The weights of the
-// stage (taps x NT x KC) arrive by a second TMA load as [tap][8-channel chunk][co][8].  When one
-// stage holds every input channel, the weights are loaded once per CTA and stay resident.
+// Rows of one MMA: 16 halo positions along x x 8 along y of one z-slice (128 voxels); K: 16 input
+// channels; columns: for a 3 x 3 x 3 stencil the NT output channels of the three x-taps of one
+// (dz, dy), N = 3 NT.  Row (x', y) then holds, in column block dx, the (dz, dy, dx) terms of input
+// x' for all (dz, dy), and output x = x' - dx + 1 is the sum over dx of row x + dx, block dx: the
+// epilogue adds the three blocks with lane shuffles, and 14 of the 16 positions are outputs.  So a
+// tile is 14 x 8 x ZT output voxels and NT channels, and nine MMAs per slice and K step replace 27.
+// The CTA stages the tile's input halo (16 x 10 x (ZT + 2) voxels, KC channels) with one TMA load
+// in the layout [8-channel chunk][z][y][x][8 channels]: a core matrix (8 voxels consecutive in x,
+// 16 bytes each) is contiguous, and the operand of (dz, dy) and slice zs is the same K-major layout
+// ((zs + dz) 10 + dy) 16 rows further in.  Shifting the descriptor replaces the im2col copy; the
+// zero padding is the TMA's out-of-range fill.  The weights of the stage (taps x NT x KC) arrive by
+// a second TMA load as [8-channel chunk][tap][co][8], so the rows (dx, co) of one (dz, dy) are
+// consecutive.  When one stage holds every input channel, the weights are loaded once per CTA and
+// stay resident.  A 1 x 1 x 1 convolution uses the same tile without halo (16 x 8 outputs, N = NT).
+// For channel tiles NT > 32 (where three column blocks leave room for one slice only) the kernel
+// takes the other tiling (MODE 0): rows 8 along x x 16 along y, a 10 x 18 x (ZT + 2) halo, one MMA
+// per tap with N = NT, the dx shift also a descriptor offset.
 //
 // Warp roles of the persistent CTA: warp 0 issues the TMA loads into a ring of stages, warp 1
 // owns tensor memory and issues the MMAs (one thread), warps 2-5 drain the accumulators
@@ -30,7 +37,8 @@
 namespace gp {
 
 constexpr int TC_THREADS = 192;      // 6 warps: TMA, MMA, 4 x epilogue
-constexpr int TC_TX = 8, TC_TY = 16; // tile extent in x and y: 128 GEMM rows per z-slice
+constexpr int TC_TX = 8, TC_TY = 16; // weight-gradient tile in x and y
+constexpr int FW_XR = 16, FW_TY = 8; // forward: MMA rows per slice, 16 along x x 8 along y
 constexpr int TC_MAX_STAGES = 4;
 constexpr size_t TC_SMEM_MAX = 227 * 1024;
 
@@ -102,7 +110,7 @@ __device__ __forceinline__ uint16_t f2bf_rn(float f) {
 
 struct ConvTcArgs {
     int D, H, W, Cout;
-    int NT, ZT, KC, nK;             // channel tile, z-slices per tile, channels per stage, stages per tile
+    int NT, N, ZT, KC, nK;          // channel tile, MMA columns, z-slices per tile, channels per stage, stages
     int tiles_x, tiles_y, n_tiles;  // spatial tiles along x and y, channel tiles
     int64_t units;                  // spatial tiles x channel tiles
     int nstages;                    // ring depth
@@ -117,13 +125,17 @@ struct ConvTcArgs {
 
 // Shared memory: [ring of stages: halo (a_stride) + weights (b_bytes, unless resident)]
 // [resident weights] [barriers: full, empty per stage; acc_full, acc_empty x 2; weights] [tmem slot]
-template <int TAPS>
+template <int TAPS, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const ConvTcArgs p) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    constexpr int R = TAPS == 27 ? 1 : 0;                 // halo width
-    constexpr int HX = TC_TX + 2 * R, HY = TC_TY + 2 * R;
+    constexpr int R = TAPS == 27 ? 1 : 0;                         // halo width
+    constexpr int NX = (TAPS == 27 && MODE == 1) ? 3 : 1;         // x-taps per MMA (column blocks)
+    constexpr int RX = MODE == 1 ? FW_XR : TC_TX;                 // MMA rows along x (then along y)
+    constexpr int RY = 128 / RX;
+    constexpr int HX = MODE == 1 ? RX : RX + 2 * R, HY = RY + 2 * R;   // halo box in x and y
+    constexpr int TXO = MODE == 1 ? RX - 2 * R : RX;              // outputs per tile along x
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = p.nstages;
     const uint32_t stage_bytes = p.a_stride + (p.b_resident ? 0u : p.b_bytes);
@@ -171,8 +183,8 @@ conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     if (ok && !mbar_wait(&empty[s], ph ^ 1u)) ok = false;
                     const uint32_t dst = smem_u32(sm + (size_t)s * stage_bytes);
                     mbar_arrive_expect_tx(&full[s], p.a_bytes + (p.b_resident ? 0u : p.b_bytes));
-                    tma_load_5d(dst, &tmA, 0, tx * TC_TX - R, ty * TC_TY - R, tz * p.ZT - R, k * (p.KC / 8), &full[s]);
-                    if (!p.b_resident) tma_load_4d(dst + p.a_stride, &tmB, 0, nt * p.NT, k * (p.KC / 8), 0, &full[s]);
+                    tma_load_5d(dst, &tmA, 0, tx * TXO - R, ty * RY - R, tz * p.ZT - R, k * (p.KC / 8), &full[s]);
+                    if (!p.b_resident) tma_load_4d(dst + p.a_stride, &tmB, 0, nt * p.NT, 0, k * (p.KC / 8), &full[s]);
                     if (++s == NS) { s = 0; ph ^= 1u; }
                 }
             }
@@ -188,22 +200,23 @@ conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = tc_idesc(p.NT, 128);
+            const uint32_t idesc = tc_idesc(p.N, 128);
             const uint32_t lboA = p.a_bytes / (p.KC / 8);        // one 8-channel chunk of the halo
-            const uint32_t lboB = (uint32_t)p.NT * 16;
+            const uint32_t lboB = (uint32_t)(TAPS * p.NT * 16);  // one 8-channel chunk of the weights
             if (p.b_resident && ok && !mbar_wait(wbar, 0)) ok = false;
             int s = 0, ab = 0;
             uint32_t ph = 0, aph = 0;
             for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
                 if (ok && !mbar_wait(&acc_empty[ab], aph ^ 1u)) ok = false;
                 tc_fence_after();
-                const uint32_t dcol = tmem + (uint32_t)(ab * p.ZT * p.NT);
+                const uint32_t dcol = tmem + (uint32_t)(ab * p.ZT * p.N);
                 for (int k = 0; k < p.nK; ++k) {
                     if (ok && !mbar_wait(&full[s], ph)) ok = false;
                     tc_fence_after();
                     const uint32_t aaddr = smem_u32(sm + (size_t)s * stage_bytes);
                     const uint32_t baddr = p.b_resident ? smem_u32(bres) : aaddr + p.a_stride;
-                    const uint64_t a0 = smem_desc(aaddr, lboA, HX * 16);
+                    // 8-row groups: MODE 1 (x-octet, y) 128 bytes apart; MODE 0 one y-row apart
+                    const uint64_t a0 = smem_desc(aaddr, lboA, MODE == 1 ? 128 : HX * 16);
                     const uint64_t b0 = smem_desc(baddr, lboB, 128);
                     for (int zs = 0; zs < p.ZT; ++zs) {
                         const uint64_t az = a0 + (uint64_t)(zs * HY * HX);      // 16-byte units
@@ -211,12 +224,15 @@ conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                             const uint64_t ak = az + (uint64_t)(kk * 2 * (lboA >> 4));
                             const uint64_t bk = b0 + (uint64_t)(kk * 2 * (lboB >> 4));
 #pragma unroll
-                            for (int t = 0; t < TAPS; ++t) {
-                                const int dz = TAPS == 27 ? t / 9 : 0, dy = TAPS == 27 ? (t / 3) % 3 : 0,
-                                          dx = TAPS == 27 ? t % 3 : 0;
+                            for (int g = 0; g < TAPS / NX; ++g) {   // MODE 1: g = 3 dz + dy, taps 3g ... 3g + 2
+                                int dz = 0, dy = 0, dx = 0;
+                                if (TAPS == 27) {
+                                    if (MODE == 1) { dz = g / 3; dy = g % 3; }
+                                    else { dz = g / 9; dy = (g / 3) % 3; dx = g % 3; }
+                                }
                                 const uint64_t at = ak + (uint64_t)((dz * HY + dy) * HX + dx);
-                                const uint64_t bt = bk + (uint64_t)(t * (p.KC / 8) * (lboB >> 4));
-                                tc_mma(dcol + (uint32_t)(zs * p.NT), at, bt, idesc, (k | kk | t) != 0 ? 1u : 0u);
+                                const uint64_t bt = bk + (uint64_t)(g * NX * p.NT);
+                                tc_mma(dcol + (uint32_t)(zs * p.N), at, bt, idesc, (k | kk | g) != 0 ? 1u : 0u);
                             }
                         }
                     }
@@ -228,10 +244,12 @@ conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             }
         }
     } else {
-        // ---- epilogue: TMEM lanes 32 q ... 32 q + 31, q = warp mod 4; lane m <-> voxel (m % 8, m / 8)
+        // ---- epilogue: TMEM lanes 32 q ... 32 q + 31, q = warp mod 4; lane m <-> row position
+        // (m % RX, m / RX); in MODE 1 the 16 lanes of a y-row are consecutive, so rows x + 1, x + 2
+        // are the lanes above
         const int q = warp & 3;
         const int m = 32 * q + lane;
-        const int lx = m & 7, ly = m >> 3;
+        const int lx = m % RX, ly = m / RX;
         int ab = 0;
         uint32_t aph = 0;
         for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
@@ -241,20 +259,32 @@ conv3d_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             const int tz = (int)(st / ntile_xy);
             if (ok && !mbar_wait(&acc_full[ab], aph)) ok = false;
             tc_fence_after();
-            const int x = tx * TC_TX + lx, y = ty * TC_TY + ly;
+            const int x = tx * TXO + lx, y = ty * RY + ly;
             const int n0 = nt * p.NT;
             for (int zs = 0; zs < p.ZT; ++zs) {
                 const int z = tz * p.ZT + zs;
-                const bool inb = x < p.W && y < p.H && z < p.D;
+                const bool inb = lx < TXO && x < p.W && y < p.H && z < p.D;
                 const int64_t o = inb ? (((int64_t)z * p.H + y) * p.W + x) * p.Cout + n0 : 0;
                 for (int c0 = 0; c0 < p.NT; c0 += 16) {
+                    const uint32_t col = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * p.ZT * p.N + zs * p.N + c0);
                     uint32_t r[16];
-                    tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * p.ZT * p.NT + zs * p.NT + c0), r);
+                    float v[16];
+                    tc_ld16(col, r);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                    if (NX == 3) {
+#pragma unroll
+                        for (int dx = 1; dx < 3; ++dx) {
+                            tc_ld16(col + (uint32_t)(dx * p.NT), r);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) v[i] += __shfl_down_sync(0xffffffffu, __uint_as_float(r[i]), dx);
+                        }
+                    }
                     if (inb) {
                         uint32_t pk[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            float o0 = __uint_as_float(r[2 * i]), o1 = __uint_as_float(r[2 * i + 1]);
+                            float o0 = v[2 * i], o1 = v[2 * i + 1];
                             if (p.bias) { o0 += p.bias[n0 + c0 + 2 * i]; o1 += p.bias[n0 + c0 + 2 * i + 1]; }
                             if (p.relu) { o0 = fmaxf(o0, 0.f); o1 = fmaxf(o1, 0.f); }
                             pk[i] = (uint32_t)f2bf_rn(o0) | ((uint32_t)f2bf_rn(o1) << 16);
@@ -321,19 +351,23 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
     auto enc = conv_encoder();
     if (!enc) return cudaErrorNotSupported;
     const int R = taps == 27 ? 1 : 0;
-    const int HX = TC_TX + 2 * R, HY = TC_TY + 2 * R;
+    const int MODE = (taps == 1 || NT <= 32) ? 1 : 0;
+    const int NX = (taps == 27 && MODE == 1) ? 3 : 1;
+    const int RX = MODE == 1 ? FW_XR : TC_TX, RY = 128 / RX;
+    const int HX = MODE == 1 ? RX : RX + 2 * R, HY = RY + 2 * R, TXO = MODE == 1 ? RX - 2 * R : RX;
+    const int N = NX * NT;
     const int sms = device_sms();
-    const int tiles_x = (W + TC_TX - 1) / TC_TX, tiles_y = (H + TC_TY - 1) / TC_TY;
+    const int tiles_x = (W + TXO - 1) / TXO, tiles_y = (H + RY - 1) / RY;
     const int n_tiles = Cout / NT;
     const size_t bar_bytes = 8 * (2 * TC_MAX_STAGES + 5) + 16;
 
     // z-slices per tile: the largest that keeps at least one unit per SM (two accumulator buffers
-    // of ZT x NT columns in the 512 of tensor memory); then the most channels per stage that let
+    // of ZT x N columns in the 512 of tensor memory); then the most channels per stage that let
     // two stages fit in shared memory.
     ConvTcArgs a{};
     int ZT = 8;
-    while (ZT > 1 && (2 * ZT * NT > 512 || (int64_t)((D + ZT - 1) / ZT) * tiles_x * tiles_y * n_tiles < sms)) ZT >>= 1;
-    if (2 * ZT * NT > 512) return cudaErrorNotSupported;
+    while (ZT > 1 && (2 * ZT * N > 512 || (int64_t)((D + ZT - 1) / ZT) * tiles_x * tiles_y * n_tiles < sms)) ZT >>= 1;
+    if (2 * ZT * N > 512) return cudaErrorNotSupported;
     int KC = 0;
     for (;;) {
         for (int kc = Cin; kc >= 16; kc -= 16) {
@@ -350,14 +384,14 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
     }
     if (KC == 0) return cudaErrorNotSupported;
     a.D = D; a.H = H; a.W = W; a.Cout = Cout;
-    a.NT = NT; a.ZT = ZT; a.KC = KC; a.nK = Cin / KC;
+    a.NT = NT; a.N = N; a.ZT = ZT; a.KC = KC; a.nK = Cin / KC;
     a.tiles_x = tiles_x; a.tiles_y = tiles_y; a.n_tiles = n_tiles;
     a.units = (int64_t)((D + ZT - 1) / ZT) * tiles_x * tiles_y * n_tiles;
     a.a_bytes = (uint32_t)(16 * HX * HY * (ZT + 2 * R) * (KC / 8));
     a.a_stride = (a.a_bytes + 1023u) & ~1023u;
     a.b_bytes = (uint32_t)(taps * NT * KC * 2);
     a.b_resident = (KC == Cin && n_tiles == 1) ? 1 : 0;
-    a.tmem_cols = tmem_columns(2 * ZT * NT);
+    a.tmem_cols = tmem_columns(2 * ZT * N);
     a.relu = relu;
     a.bias = bias;
     a.out = out;
@@ -380,18 +414,19 @@ cudaError_t launch_conv3d_fwd_tc(const uint16_t* in, int D, int H, int W, int Ci
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorNotSupported;
     }
-    // weights w[co][tap][ci]: dims (8 channels, co, channel chunk, tap), box (8, NT, KC / 8, taps)
+    // weights w[co][tap][ci]: dims (8 channels, co, tap, channel chunk), box (8, NT, taps, KC / 8)
     {
-        cuuint64_t dims[4] = {8, (cuuint64_t)Cout, (cuuint64_t)(Cin / 8), (cuuint64_t)taps};
-        cuuint64_t strides[3] = {(cuuint64_t)taps * Cin * 2, 16, (cuuint64_t)Cin * 2};
-        cuuint32_t box[4] = {8, (cuuint32_t)NT, (cuuint32_t)(KC / 8), (cuuint32_t)taps};
+        cuuint64_t dims[4] = {8, (cuuint64_t)Cout, (cuuint64_t)taps, (cuuint64_t)(Cin / 8)};
+        cuuint64_t strides[3] = {(cuuint64_t)taps * Cin * 2, (cuuint64_t)Cin * 2, 16};
+        cuuint32_t box[4] = {8, (cuuint32_t)NT, (cuuint32_t)taps, (cuuint32_t)(KC / 8)};
         cuuint32_t es[4] = {1, 1, 1, 1};
         if (enc(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(w), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorNotSupported;
     }
-    auto kern = taps == 27 ? conv3d_fwd_tc_kernel<27> : conv3d_fwd_tc_kernel<1>;
+    auto kern = taps == 1 ? conv3d_fwd_tc_kernel<1, 1>
+                          : (MODE == 1 ? conv3d_fwd_tc_kernel<27, 1> : conv3d_fwd_tc_kernel<27, 0>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = a.units < sms ? a.units : sms;
