@@ -5,37 +5,54 @@
 // Work decomposition: one CTA per tile of 256 Gaussians, one thread per Gaussian.  The CTA
 // walks all sensors in chunks of 32: warp 0 forms the 32 FP64 (tile, sensor) references, the
 // CTA stages each sensor's residual band (the samples the tile can touch) in shared memory,
-// and every thread gathers its own pair windows from those bands.  Each Gaussian's sums over
-// sensors are Kahan-compensated in registers and written once: no atomics of any kind.
+// and every thread gathers its own pair windows from those bands.  Each Gaussian's sums over a
+// chunk's sensors are FP32, Kahan-compensated across chunks in registers, and written once: no
+// global atomics.  Free-centre Gaussians are taken in the order of their window length (a
+// counting sort of the tile in shared memory), so the 32 threads of a warp walk windows of about
+// the same length.
 #include "gpair_internal.cuh"
 
 namespace gp {
 
 constexpr int ADJ_THREADS = TILE;
 constexpr int ADJ_SC = 32;   // sensors staged per chunk
+constexpr int ADJ_KEYS = 64; // window-length keys of the free-centre ordering
 
 
 
 // Window sums of one pair: s1 = sum dl d e (amplitude gradient); with FULL also s0 = sum dl e,
 // s2 = sum dl d^2 e, s3 = sum dl d^3 e (centre and width gradients).  src[m] is the residual at
-// sample n0 + m; d = phi - m Delta is the pair's phase there.
+// sample n0 + m; d = phi - m Delta is the pair's phase there.  Samples go two at a time through
+// packed FP32 pairs (mul/add/fma .f32x2), the even and odd samples in the two halves of each
+// accumulator; an odd window's last pair has its second residual set to zero.
 template <bool FULL>
 __device__ __forceinline__ void window_sums(const float* __restrict__ src, int m_lo, int m_hi, float phi,
                                             float Delta, float c2, float& s0, float& s1, float& s2, float& s3) {
-    for (int m = m_lo; m <= m_hi; ++m) {
-        const float d = fmaf(-(float)m, Delta, phi);
-        const float e = ex2_approx(d * d * c2);
-        const float u = src[m] * e;
+    float2 fm = make_float2((float)m_lo, (float)(m_lo + 1));     // m as floats, stepped exactly
+    const float2 two = make_float2(2.f, 2.f), nD = make_float2(-Delta, -Delta), cc = make_float2(c2, c2);
+    const float2 ph = make_float2(phi, phi);
+    float2 S0 = make_float2(0.f, 0.f), S1 = S0, S2 = S0, S3 = S0;
+    for (int m = m_lo; m <= m_hi; m += 2, fm = __fadd2_rn(fm, two)) {
+        const float2 d = __ffma2_rn(fm, nD, ph);
+        const float2 E = __fmul2_rn(__fmul2_rn(d, d), cc);
+        const float x0 = src[m], x1 = m + 1 <= m_hi ? src[m + 1] : 0.f;
+        const float2 u = __fmul2_rn(make_float2(x0, x1), make_float2(ex2_approx(E.x), ex2_approx(E.y)));
         if (FULL) {
-            const float ud = u * d;
-            s0 += u;
-            s1 += ud;
-            const float udd = ud * d;
-            s2 += udd;
-            s3 = fmaf(udd, d, s3);
+            const float2 ud = __fmul2_rn(u, d);
+            const float2 udd = __fmul2_rn(ud, d);
+            S0 = __fadd2_rn(S0, u);
+            S1 = __fadd2_rn(S1, ud);
+            S2 = __fadd2_rn(S2, udd);
+            S3 = __ffma2_rn(udd, d, S3);
         } else {
-            s1 = fmaf(u, d, s1);
+            S1 = __ffma2_rn(u, d, S1);
         }
+    }
+    s1 += S1.x + S1.y;
+    if (FULL) {
+        s0 += S0.x + S0.y;
+        s2 += S2.x + S2.y;
+        s3 += S3.x + S3.y;
     }
 }
 
@@ -46,10 +63,28 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
     extern __shared__ __align__(16) float bands[];   // [ADJ_SC][LBA]
     __shared__ PairRef refs[ADJ_SC];
     __shared__ int nbs[ADJ_SC];
+    __shared__ int hist[ADJ_KEYS], perm[ADJ_THREADS];
 
     const int64_t t = blockIdx.x;
-    const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
+    const int l0 = threadIdx.x, warp = l0 >> 5, lane = l0 & 31;
     const TileInfo rt = ti[t];
+    // free centres: thread l0 takes the tile's Gaussian perm[l0], in the order of window length
+    // (2 k sigma / Delta, clamped to the key range; invalid entries last)
+    int l = l0;
+    if (!GRID) {
+        const int64_t i0 = t * TILE + l0;
+        const int key = i0 < g.M ? min(ADJ_KEYS - 1, (int)(2.f * a.k * g.sg[i0] * a.invDelta)) : ADJ_KEYS - 1;
+        for (int q = l0; q < ADJ_KEYS; q += ADJ_THREADS) hist[q] = 0;
+        __syncthreads();
+        const int rank = atomicAdd(&hist[key], 1);
+        __syncthreads();
+        if (l0 == 0)
+            for (int q = 0, acc = 0; q < ADJ_KEYS; ++q) { const int c = hist[q]; hist[q] = acc; acc += c; }
+        __syncthreads();
+        perm[hist[key] + rank] = l0;
+        __syncthreads();
+        l = perm[l0];
+    }
 
     // This thread's Gaussian: index, amplitude, width and offset from the tile reference.
     bool valid;
@@ -78,6 +113,7 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
         c0x = rt.c0x; c0y = rt.c0y; c0z = rt.c0z;
     }
     const float c2 = -0.72134752044448170368f / (sig * sig);   // -log2(e) / (2 sigma^2)
+    const float inv_s2 = 1.f / (sig * sig), inv_s3 = inv_s2 / sig;
     const float ks = a.k * sig;
     const float Delta = a.Delta, invDelta = a.invDelta;
     const float reach = rt.rad + a.k * rt.smax;                // farthest |d| offset in the tile
@@ -92,12 +128,16 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
             nbs[lane] = (r.n0 + (int)floorf((r.phi0 - reach) * invDelta) - 2) & ~3;
         }
         __syncthreads();
-        for (int idx = l; idx < nsc * LBA; idx += ADJ_THREADS) {
-            const int q = idx / LBA, n = nbs[q] + (idx - q * LBA);
-            bands[idx] = (n >= 0 && n < a.Nt) ? delta[(size_t)(j0 + q) * a.Nt + n] : 0.f;
+        for (int q = 0; q < nsc; ++q) {
+            const float* dj = delta + (size_t)(j0 + q) * a.Nt;
+            for (int c = l0; c < LBA; c += ADJ_THREADS) {
+                const int n = nbs[q] + c;
+                bands[q * LBA + c] = (n >= 0 && n < a.Nt) ? dj[n] : 0.f;
+            }
         }
         __syncthreads();
         if (valid) {
+            float aA = 0.f, aX = 0.f, aY = 0.f, aZ = 0.f, aS = 0.f;   // FP32 over the chunk
             for (int q = 0; q < nsc; ++q) {
                 const PairRef r = refs[q];
                 float invR, phi;
@@ -111,16 +151,19 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
                 else
                     window_sums<FULL>(delta + (size_t)(j0 + q) * a.Nt + r.n0, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
                 const float inv2R = 0.5f * invR;
-                kA.add(s1 * inv2R);
+                aA = fmaf(s1, inv2R, aA);
                 if (FULL) {
                     const float wA = Ai * inv2R;
-                    const float gR = wA * (s0 - s2 / (sig * sig)) - wA * s1 * invR;
-                    kX.add(gR * (r.v0x + dx) * invR);
-                    kY.add(gR * (r.v0y + dy) * invR);
-                    kZ.add(gR * (r.v0z + dz) * invR);
-                    kS.add(wA * s3 / (sig * sig * sig));
+                    const float gR = wA * (s0 - s2 * inv_s2) - wA * s1 * invR;
+                    const float gRi = gR * invR;
+                    aX = fmaf(gRi, r.v0x + dx, aX);
+                    aY = fmaf(gRi, r.v0y + dy, aY);
+                    aZ = fmaf(gRi, r.v0z + dz, aZ);
+                    aS = fmaf(wA * s3, inv_s3, aS);
                 }
             }
+            kA.add(aA);
+            if (FULL) { kX.add(aX); kY.add(aY); kZ.add(aZ); kS.add(aS); }
         }
         __syncthreads();
     }

@@ -403,16 +403,46 @@ def conv_bench(dims, cin, cout, modes=(1, 2, 0), reps=20, seed=0, which="fwd"):
     return out
 
 
+def train_bench(dims, reps=20, seed=0):
+    """Time the network's training step (forward, backward, Adam) and its prediction on random
+    input and target volumes, after three warm-up steps.  Returns (train ms, predict ms)."""
+    net = UNet3D(dims, seed=seed)
+    n = dims[0] * dims[1] * dims[2]
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.rand(n, device="cuda", generator=g)
+    t = torch.rand(n, device="cuda", generator=g)
+    for _ in range(3):
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    for _ in range(reps):
+        net.train_step(x, t, 1e-4)
+    e1.record()
+    for _ in range(reps):
+        net.predict(x)
+    e2.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, e1.elapsed_time(e2) / reps
+
+
 if __name__ == "__main__":
     import argparse
     import json
 
-    ap = argparse.ArgumentParser(description="time one U-Net convolution layer on each kernel path")
-    ap.add_argument("--conv-bench", nargs=5, type=int, metavar=("D", "H", "W", "CIN", "COUT"), required=True)
+    ap = argparse.ArgumentParser(description="time one U-Net convolution layer on each kernel path, or the "
+                                             "whole training step")
+    g = ap.add_mutually_exclusive_group(required=True)
+    g.add_argument("--conv-bench", nargs=5, type=int, metavar=("D", "H", "W", "CIN", "COUT"))
+    g.add_argument("--train-bench", nargs=3, type=int, metavar=("D", "H", "W"))
     ap.add_argument("--modes", type=int, nargs="+", default=[1, 2, 0])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--pass", dest="which", choices=["fwd", "dgrad", "wgrad"], default="fwd")
     a = ap.parse_args()
-    D, H, W, cin, cout = a.conv_bench
-    res = conv_bench((D, H, W), cin, cout, tuple(a.modes), a.reps, which=a.which)
-    print(json.dumps({f"mode{m}": {"ms": v[0], "TFLOP/s": v[1]} for m, v in res.items()}))
+    if a.train_bench:
+        tr, pr = train_bench(tuple(a.train_bench), a.reps)
+        print(json.dumps({"train_step_ms": tr, "predict_ms": pr}))
+    else:
+        D, H, W, cin, cout = a.conv_bench
+        res = conv_bench((D, H, W), cin, cout, tuple(a.modes), a.reps, which=a.which)
+        print(json.dumps({f"mode{m}": {"ms": v[0], "TFLOP/s": v[1]} for m, v in res.items()}))
