@@ -122,11 +122,14 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
                 const TileInfo rt = ti[sl.t_begin + t];
                 const PairRef r = ref_doubled(make_ref(rt.c0x, rt.c0y, rt.c0z, sx, sy, sz, a));
                 const int ybase = r.n0 - w;                    // band index of sample n0 + m is ybase + m
-#pragma unroll 1
-                for (int l = 0; l < TILE; ++l) {
+                // one window: positions to walk Q (0: skip), its first sample's band row y0, the
+                // positions [qa, qa + span) this pass keeps (its band, inside the record; none when
+                // the window lies wholly in another pass's band), d_0, A / 2R and the exponent scale
+                struct Win { int Q, y0, qa, span; float d, wR, c2; };
+                auto window = [&](int l) {
                     const FfGauss G = S.tile[b][l];
-                    const int Q = (int)G.e.w;                  // positions to walk (0: skip)
-                    if (Q == 0) continue;
+                    Win w;
+                    w.Q = (int)G.e.w;
                     float invR, phi;
                     pair_phase_pre(r, G.o.x, G.o.y, G.o.z, G.o.w, invR, phi);
                     const float tt = phi * invDelta;
@@ -134,19 +137,29 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
                     const float uhi = __fadd_rd(tt + G.e.z, FF_MAGIC);      // MAGIC + last window sample
                     const int m0 = __float_as_int(ulo) - FF_MAGIC_BITS;
                     const int cnt = __float_as_int(uhi) - __float_as_int(ulo) + 1;
-                    float d = fmaf(-(ulo - FF_MAGIC), Delta, phi);            // d_0
-                    // the window positions this pass keeps (its band, inside the record); none when
-                    // the window lies wholly in another pass's band
-                    const int y0 = ybase + m0;
-                    const int qa = max(0, -y0), span = max(0, min(cnt, LBe - y0) - qa);
-                    const float wR = G.e.x * invR;                           // A / 2R
-                    const float c2 = G.e.y;
+                    w.d = fmaf(-(ulo - FF_MAGIC), Delta, phi);
+                    w.y0 = ybase + m0;
+                    w.qa = max(0, -w.y0);
+                    w.span = max(0, min(cnt, LBe - w.y0) - w.qa);
+                    w.wR = G.e.x * invR;
+                    w.c2 = G.e.y;
+                    return w;
+                };
+                // the next Gaussian's window is formed while this one is walked
+                Win cur = window(0);
+#pragma unroll 1
+                for (int l = 0; l < TILE; ++l) {
+                    const Win nxt = window(l + 1 < TILE ? l + 1 : l);
+                    if (cur.Q > 0) {
+                        float d = cur.d;
 #pragma unroll 4
-                    for (int q = 0; q < Q; ++q) {
-                        const float v = wR * d * ex2_approx(d * d * c2);
-                        if ((unsigned)(q - qa) < (unsigned)span) Y[(y0 + q) * 32 + lane] += v;
-                        d -= Delta;
+                        for (int q = 0; q < cur.Q; ++q) {
+                            const float v = cur.wR * d * ex2_approx(d * d * cur.c2);
+                            if ((unsigned)(q - cur.qa) < (unsigned)cur.span) Y[(cur.y0 + q) * 32 + lane] += v;
+                            d -= Delta;
+                        }
                     }
+                    cur = nxt;
                 }
             }
             __syncthreads();      // tile t's buffer is free; tile t + 1 is staged
