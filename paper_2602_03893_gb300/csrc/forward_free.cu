@@ -24,7 +24,7 @@
 
 namespace gp {
 
-constexpr int FF_MAXW = 4;            // warps per CTA, at most
+constexpr int FF_MAXW = 8;            // warps per CTA, at most
 constexpr int FF_THREADS_MAX = FF_MAXW * 32;
 
 // Staged constants of one Gaussian (uniform over the lanes): 8 floats as two float4.

@@ -24,6 +24,8 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
 size_t fwd_free_smem(int NW, int LB);
+size_t spatial_order_bytes(int64_t M);
+cudaError_t launch_spatial_order(const GaussDev& g, void* scratch, GaussDev& gp, cudaStream_t st);
 cudaError_t launch_forward_free(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
                                 float* partial, int2* rows, int PL, int LB, int NW, cudaStream_t st);
 cudaError_t launch_slab_reduce_rows(const ArrDev& a, const float* partial, const int2* rows, int S, int PL, float* y,
@@ -224,6 +226,7 @@ struct FwdPlan {
     bool free_lanes;       // SoA mode: the sensor-lane direct kernel (slabs of tile ranges)
     int NW, NZ;            // warps per CTA of the lanes kernels; moment-band bins (grid)
     size_t off_ti, off_si, off_rows, off_part, bytes;
+    size_t off_sort;       // free-centre lanes plan: the spatial order's scratch (after the rest)
 };
 
 void plan_offsets(FwdPlan& p, const GaussDev& g, const ArrDev& a) {
@@ -396,7 +399,7 @@ bool plan_forward_lanes(const GaussDev& g, const ArrDev& a, const MomentTable& T
     return true;
 }
 
-constexpr int FREE_LANES_WARPS = 4;    // warps (sensor groups of 32) per CTA of the free-centre kernel
+constexpr int FREE_LANES_WARPS = 8;    // warps (sensor groups of 32) per CTA of the free-centre kernel
 
 // Free-centre Gaussians with the sensor-lane direct kernel: slabs of contiguous tile ranges,
 // enough of them for about four CTAs per SM while the partial rows (capacity N_t, rounded up to
@@ -419,6 +422,8 @@ bool plan_forward_free(const GaussDev& g, const ArrDev& a, FwdPlan& p) {
     if (p.LB < 64) return false;
     p.free_lanes = true;
     plan_offsets(p, g, a);
+    p.off_sort = p.bytes;
+    p.bytes += align256(spatial_order_bytes(g.M));
     return true;
 }
 
@@ -471,10 +476,13 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
     memset(&map, 0, sizeof(map));
     cudaError_t e = cudaSuccess;
     if (p.free_lanes) {
-        e = launch_tile_info(g, ti, st);
-        if (e == cudaSuccess) e = launch_slab_info_soa(g, g.ntiles, p.tiles_per_slab, p.S, si, st);
+        // the Gaussians in the Morton order of their centres: tiles of nearby Gaussians, short bands
+        GaussDev gp;
+        e = launch_spatial_order(g, base + p.off_sort, gp, st);
+        if (e == cudaSuccess) e = launch_tile_info(gp, ti, st);
+        if (e == cudaSuccess) e = launch_slab_info_soa(gp, gp.ntiles, p.tiles_per_slab, p.S, si, st);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess) e = launch_forward_free(g, a, ti, si, p.S, part, rows, p.PL, p.LB, p.NW, st);
+        if (e == cudaSuccess) e = launch_forward_free(gp, a, ti, si, p.S, part, rows, p.PL, p.LB, p.NW, st);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
         if (e == cudaSuccess) e = launch_slab_reduce_rows(a, part, rows, p.S, p.PL, y, st);
         return cuda_status(e);
