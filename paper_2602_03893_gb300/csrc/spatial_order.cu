@@ -54,16 +54,22 @@ __global__ void so_box_partial_kernel(GaussDev g, float* __restrict__ part) {
     if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-__global__ void so_box_final_kernel(const float* __restrict__ part, int nb, float* __restrict__ box) {
-    if (threadIdx.x < 6) {
-        const bool lo = threadIdx.x < 3;
-        float v = lo ? FLT_MAX : -FLT_MAX;
-        for (int b = 0; b < nb; ++b) {
-            const float p = part[b * 6 + threadIdx.x];
-            v = lo ? fminf(v, p) : fmaxf(v, p);
-        }
-        box[threadIdx.x] = v;
+// One block of SO_BB_BLOCKS threads: thread b takes block b's partials, then a tree.
+__global__ void so_box_final_kernel(const float* __restrict__ part, float* __restrict__ box) {
+    __shared__ float red[6][SO_BB_BLOCKS];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = part[threadIdx.x * 6 + q];
+    __syncthreads();
+    for (int s = SO_BB_BLOCKS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                red[q][threadIdx.x] = fminf(red[q][threadIdx.x], red[q][threadIdx.x + s]);
+                red[3 + q][threadIdx.x] = fmaxf(red[3 + q][threadIdx.x], red[3 + q][threadIdx.x + s]);
+            }
+        __syncthreads();
     }
+    if (threadIdx.x < 6) box[threadIdx.x] = red[threadIdx.x][0];
 }
 
 // the axis bits spread three apart (bit b to bit 3b), for interleaving x, y, z from the lowest bit
@@ -106,27 +112,28 @@ __global__ void so_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int
     for (int d = threadIdx.x; d < SO_RADIX; d += SO_THREADS) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// Step 2: exclusive scan of the counts in (digit, block) order, one block of 1024 threads.
-__global__ void so_scan_kernel(int* __restrict__ hist, int n) {
-    __shared__ int part[1024];
-    const int per = (n + 1023) / 1024;
-    const int q0 = threadIdx.x * per, q1 = min(n, q0 + per);
+// Step 2: exclusive scan of the counts in (digit, block) order, one block with a thread per
+// digit: thread d scans its own row of per-block counts, then the block scans the digit totals.
+__global__ void so_scan_kernel(int* __restrict__ hist, int nb) {
+    __shared__ int tot[SO_RADIX];
+    const int d = threadIdx.x;
+    int* row = hist + (size_t)d * nb;
     int s = 0;
-    for (int q = q0; q < q1; ++q) s += hist[q];
-    part[threadIdx.x] = s;
+    for (int b = 0; b < nb; ++b) {
+        const int c = row[b];
+        row[b] = s;
+        s += c;
+    }
+    tot[d] = s;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {        // inclusive scan of the segment sums
-        const int v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+    for (int off = 1; off < SO_RADIX; off <<= 1) {    // inclusive scan of the digit totals
+        const int v = d >= off ? tot[d - off] : 0;
         __syncthreads();
-        part[threadIdx.x] += v;
+        tot[d] += v;
         __syncthreads();
     }
-    int acc = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (int q = q0; q < q1; ++q) {
-        const int c = hist[q];
-        hist[q] = acc;
-        acc += c;
-    }
+    const int before = d ? tot[d - 1] : 0;
+    for (int b = 0; b < nb; ++b) row[b] += before;
 }
 
 // Step 3: stable scatter.  The block takes its keys 256 at a time in index order; inside a warp
@@ -206,13 +213,13 @@ cudaError_t launch_spatial_order(const GaussDev& g, void* scratch, GaussDev& gp,
     float* out = reinterpret_cast<float*>(p + 4 * a + align256_sz((size_t)SO_RADIX * nb * 4) +
                                           align256_sz((size_t)(SO_BB_BLOCKS + 1) * 6 * 4));
     so_box_partial_kernel<<<SO_BB_BLOCKS, SO_THREADS, 0, st>>>(g, boxp);
-    so_box_final_kernel<<<1, 32, 0, st>>>(boxp, SO_BB_BLOCKS, box);
+    so_box_final_kernel<<<1, SO_BB_BLOCKS, 0, st>>>(boxp, box);
     const unsigned eb = (unsigned)((M + 255) / 256);
     so_keys_kernel<<<eb, 256, 0, st>>>(g, box, keys[0], vals[0]);
     for (int pass = 0; pass < SO_PASSES; ++pass) {
         const int in = pass & 1;
         so_hist_kernel<<<nb, SO_THREADS, 0, st>>>(keys[in], M, SO_DIGIT * pass, hist);
-        so_scan_kernel<<<1, 1024, 0, st>>>(hist, SO_RADIX * nb);
+        so_scan_kernel<<<1, SO_RADIX, 0, st>>>(hist, nb);
         so_scatter_kernel<<<nb, SO_THREADS, 0, st>>>(keys[in], vals[in], M, SO_DIGIT * pass, hist, keys[in ^ 1],
                                                      vals[in ^ 1]);
     }
