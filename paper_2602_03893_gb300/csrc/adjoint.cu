@@ -17,6 +17,8 @@ namespace gp {
 constexpr int ADJ_THREADS = TILE;
 constexpr int ADJ_SC = 32;   // sensors staged per chunk
 constexpr int ADJ_KEYS = 64; // window-length keys of the free-centre ordering
+constexpr float ADJ_MAGIC = 12582912.0f;    // 1.5 * 2^23: x + MAGIC, rounded up (down), holds ceil(x) (floor(x))
+constexpr int ADJ_MAGIC_BITS = 0x4B400000;
 
 
 
@@ -56,8 +58,59 @@ __device__ __forceinline__ void window_sums(const float* __restrict__ src, int m
     }
 }
 
+// The same sums over a window held in a staged band, in the scaled phase s = sc d
+// (sc = sqrt(log2(e) / 2) / sigma, so that exp(-d^2 / 2 sigma^2) = 2^(-s^2)): S0 = sum dl e,
+// S1 = sum dl s e, S2 = sum dl s^2 e, S3 = sum dl s^3 e.  band[c] is the residual at band index
+// c; the window is [c_lo, c_hi] with s_lo the scaled phase at c_lo and step = sc Delta.  The walk
+// reads the band two samples at a time as one aligned float2, from the even index at or below
+// c_lo up to the pair holding c_hi (band[c_hi + 1] must exist): only the first and the last pair
+// can hold a sample outside the window, and only those two are masked.
+template <bool FULL>
+__device__ __forceinline__ void band_sums(const float* __restrict__ band, int c_lo, int c_hi, float s_lo, float step,
+                                          float& s0, float& s1, float& s2, float& s3) {
+    const int ca = c_lo & ~1;
+    const int NI = ((c_hi - ca) >> 1) + 1;                      // pairs walked (c_hi >= c_lo)
+    const float2* bp = reinterpret_cast<const float2*>(band + ca);
+    const float sa = (c_lo & 1) ? s_lo + step : s_lo;           // scaled phase at index ca
+    float2 s = make_float2(sa, sa - step);
+    const float2 ds = make_float2(-2.f * step, -2.f * step);
+    float2 S0 = make_float2(0.f, 0.f), S1 = S0, S2 = S0, S3 = S0;
+    auto pair = [&](float2 x) {
+        const float2 ss = __fmul2_rn(s, s);
+        const float2 u = __fmul2_rn(x, make_float2(ex2_approx(-ss.x), ex2_approx(-ss.y)));
+        if (FULL) {
+            const float2 us = __fmul2_rn(u, s);
+            const float2 uss = __fmul2_rn(us, s);
+            S0 = __fadd2_rn(S0, u);
+            S1 = __fadd2_rn(S1, us);
+            S2 = __fadd2_rn(S2, uss);
+            S3 = __ffma2_rn(uss, s, S3);
+        } else {
+            S1 = __ffma2_rn(u, s, S1);
+        }
+        s = __fadd2_rn(s, ds);
+    };
+    const int last_hi = ca + 2 * (NI - 1) + 1;                  // second index of the last pair
+    float2 x = bp[0];
+    if (c_lo & 1) x.x = 0.f;
+    if (NI == 1 && last_hi > c_hi) x.y = 0.f;
+    pair(x);
+    for (int q = 1; q < NI - 1; ++q) pair(bp[q]);
+    if (NI > 1) {
+        x = bp[NI - 1];
+        if (last_hi > c_hi) x.y = 0.f;
+        pair(x);
+    }
+    s1 += S1.x + S1.y;
+    if (FULL) {
+        s0 += S0.x + S0.y;
+        s2 += S2.x + S2.y;
+        s3 += S3.x + S3.y;
+    }
+}
+
 template <bool GRID, bool FULL>
-__global__ void __launch_bounds__(ADJ_THREADS)
+__global__ void __launch_bounds__(ADJ_THREADS, 4)
 adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* __restrict__ delta,
            float* __restrict__ gA, float* __restrict__ gc, float* __restrict__ gs, int LBA) {
     extern __shared__ __align__(16) float bands[];   // [ADJ_SC][LBA]
@@ -116,6 +169,9 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
     const float inv_s2 = 1.f / (sig * sig), inv_s3 = inv_s2 / sig;
     const float ks = a.k * sig;
     const float Delta = a.Delta, invDelta = a.invDelta;
+    const float sc = 0.84932180028801904272f / sig;             // sqrt(log2(e) / 2) / sigma
+    const float isc = 1.f / sc, step = sc * Delta;
+    const float ksi = ks * invDelta;
     const float reach = rt.rad + a.k * rt.smax;                // farthest |d| offset in the tile
 
     KahanF kA, kX, kY, kZ, kS;
@@ -142,14 +198,25 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
                 const PairRef r = refs[q];
                 float invR, phi;
                 pair_phase_fast(r, dx, dy, dz, invR, phi);
-                const int m_lo = max((int)ceilf((phi - ks) * invDelta), -r.n0);
-                const int m_hi = min((int)floorf((phi + ks) * invDelta), a.Nt - 1 - r.n0);
+                // window [w_lo, w_hi] in samples from n0 (the forward's rounding of its ends)
+                const float tt = phi * invDelta;
+                const float ulo = __fadd_ru(tt - ksi, ADJ_MAGIC), uhi = __fadd_rd(tt + ksi, ADJ_MAGIC);
+                const int w_lo = __float_as_int(ulo) - ADJ_MAGIC_BITS, w_hi = __float_as_int(uhi) - ADJ_MAGIC_BITS;
                 const int off = r.n0 - nbs[q];
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                if ((off + m_lo >= 0) && (off + m_hi < LBA))
-                    window_sums<FULL>(bands + q * LBA + off, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
-                else
-                    window_sums<FULL>(delta + (size_t)(j0 + q) * a.Nt + r.n0, m_lo, m_hi, phi, Delta, c2, s0, s1, s2, s3);
+                if (w_lo <= w_hi) {
+                    if ((off + w_lo >= 0) && (off + w_hi + 1 < LBA)) {
+                        // the band is zero outside the record: no clamp; sums in the scaled phase
+                        band_sums<FULL>(bands + q * LBA, off + w_lo, off + w_hi,
+                                        sc * fmaf(-(ulo - ADJ_MAGIC), Delta, phi), step, s0, s1, s2, s3);
+                        s1 *= isc;
+                        if (FULL) { s2 *= isc * isc; s3 *= isc * isc * isc; }
+                    } else {
+                        const int m_lo = max(w_lo, -r.n0), m_hi = min(w_hi, a.Nt - 1 - r.n0);
+                        window_sums<FULL>(delta + (size_t)(j0 + q) * a.Nt + r.n0, m_lo, m_hi, phi, Delta, c2, s0, s1,
+                                          s2, s3);
+                    }
+                }
                 const float inv2R = 0.5f * invR;
                 aA = fmaf(s1, inv2R, aA);
                 if (FULL) {

@@ -5,16 +5,30 @@
 // Work decomposition.  Gaussians come in tiles of 256 consecutive ones (with a reference point
 // and radius per tile, tile_info_soa_kernel) and tiles in slabs (contiguous tile ranges).  A CTA
 // owns one slab and NW x 32 sensors.  The CTA stages each tile's Gaussians in shared memory with
-// the per-Gaussian constants of the window (offset from the tile reference, A / 2, the
-// exponent scale -log2(e) / 2 sigma^2, k sigma / Delta, the positions to walk), double
-// buffered.  All lanes then take the same Gaussian: a lane forms its pair's phase from the FP64
-// (tile, sensor) reference and the window's first and last samples, and walks the window,
-// adding (A / 2R) d_q exp(-d_q^2 / 2 sigma^2) at d_q = d_0 - q Delta into its own signal band,
-// laid out [sample][lane] so that the 32 lanes' read-modify-writes fall in 32 banks whatever
-// samples they address.  After the slab each lane writes its band as the slab's banded partial
-// row (start sample, length); the slab reduction sums the rows per sample in fixed slab order.
-// No atomics.  A sensor whose band is longer than the shared-memory band takes several passes
-// over the slab, each keeping the next LB samples.
+// the per-Gaussian constants of the window (offset from the tile reference, the scaled weight
+// A / 2 sc, the phase scale sc = sqrt(log2(e) / 2) / sigma, k sigma / Delta, the sample pairs to
+// walk), double buffered.  All lanes then take the same Gaussian: a lane forms its pair's phase
+// from the FP64 (tile, sensor) reference and the window's first and last samples, and walks the
+// window adding (A / 2R) d_q exp(-d_q^2 / 2 sigma^2) at d_q = d_0 - q Delta into its own signal
+// band.  In the scaled phase s = sc d the term is (A / 2R sc) s 2^(-s^2).
+//
+// Band layout.  A warp's band holds rows (samples) 2i and 2i + 1 of lane l as one float2 at
+// [i][l]: the 32 lanes' 8-byte accesses fall in distinct banks whatever rows they address, and a
+// lane walks its window two samples per step with packed FP32 arithmetic (one 8-byte
+// read-modify-write, one FMUL2 for s^2, one for the weight, one FFMA2 into the band, one FADD2 for
+// the phase, two ex2).  The walk starts at the even row at or below the window's first sample;
+// only its first pair and last three pairs can hold samples outside the window, and only those
+// are masked.  When a lane's walked rows do not all lie in its band (a window across a pass
+// boundary or the record's start), the warp walks that Gaussian with every pair tested against
+// the band and the window; a window that lies wholly in another pass's samples is skipped.  Rows
+// past the band's kept entries are never written out.  The windows of the next FF_G Gaussians (phase,
+// bounds and weight: a chain of about twenty dependent operations with two MUFU operations
+// each) are formed together while the current FF_G are walked, so that their latencies overlap.
+//
+// After the slab each lane writes its band as the slab's banded partial row (start sample,
+// length); the slab reduction sums the rows per sample in fixed slab order.  No atomics.  A
+// sensor whose band is longer than the shared-memory band takes several passes over the slab,
+// each keeping the next LB samples.
 #include <cuda.h>
 
 #include <climits>
@@ -26,11 +40,13 @@ namespace gp {
 
 constexpr int FF_MAXW = 8;            // warps per CTA, at most
 constexpr int FF_THREADS_MAX = FF_MAXW * 32;
+constexpr int FF_G = 4;               // Gaussians whose windows are formed together (divides TILE)
+static_assert(TILE % FF_G == 0, "FF_G divides the tile");
 
 // Staged constants of one Gaussian (uniform over the lanes): 8 floats as two float4.
 struct FfGauss {
     float4 o;    // dx, dy, dz (offset from the tile reference), |offset|^2
-    float4 e;    // A / 2, c2 = -log2(e) / (2 sigma^2), k sigma / Delta, positions to walk (as float)
+    float4 e;    // A / (2 sc), sc = sqrt(log2(e) / 2) / sigma, k sigma / Delta, sample pairs to walk (0: skip)
 };
 struct FfHdr {
     FfGauss tile[2][TILE];
@@ -50,7 +66,8 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
     FfHdr& S = *reinterpret_cast<FfHdr*>(smem_raw);
     const int NW = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* Y = reinterpret_cast<float*>(smem_raw + FF_HDR) + (size_t)warp * LB * 32;   // [LB][32]
+    // rows 2i, 2i + 1 of this lane at Y2[i * 32] (LB is a multiple of 4)
+    float2* Y2 = reinterpret_cast<float2*>(smem_raw + FF_HDR) + (size_t)warp * (LB / 2) * 32 + lane;
 
     const int slab = blockIdx.y;
     const int j = (blockIdx.x * NW + warp) * 32 + lane;
@@ -96,13 +113,15 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
             if (i < g.M && g.A[i] != 0.f) {
                 const float dx = g.cx[i] - r.c0x, dy = g.cy[i] - r.c0y, dz = g.cz[i] - r.c0z;
                 const float sg = g.sg[i];
-                const float c2 = __fdividef(-0.72134752044448170368f, sg * sg);   // -log2(e) / (2 sigma^2)
+                const float sc = __fdividef(0.84932180028801904272f, sg);   // sqrt(log2(e) / 2) / sigma
                 const float ksi = a.k * sg * invDelta;
                 q.o = make_float4(dx, dy, dz, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                q.e = make_float4(0.5f * g.A[i], c2, ksi, floorf(2.f * ksi) + 2.f);
+                // pairs: a window holds at most floor(2 ksi) + 2 samples (rounding of its ends
+                // included) and the walk may start one row early
+                q.e = make_float4(__fdividef(0.5f * g.A[i], sc), sc, ksi, (float)(((int)floorf(2.f * ksi) + 4) >> 1));
             } else {
                 q.o = make_float4(0.f, 0.f, 0.f, 0.f);
-                q.e = make_float4(0.f, 0.f, 0.f, 0.f);    // zero positions: skipped
+                q.e = make_float4(0.f, 0.f, 0.f, 0.f);    // zero pairs: skipped
             }
             S.tile[b][l] = q;
         }
@@ -112,7 +131,7 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
         const int w = wa + pass * LB;
         const bool active = has_sensor && pass < npass_j;
         const int LBe = active ? min(LB, min(a.Nt, n_hi + 1) - w) : 0;     // band entries this pass keeps
-        for (int q = 0; q < LB; ++q) Y[q * 32 + lane] = 0.f;
+        for (int q = 0; q < LB / 2; ++q) Y2[q * 32] = make_float2(0.f, 0.f);
         if (nTiles > 0) stage(0, 0);
         __syncthreads();
         for (int t = 0; t < nTiles; ++t) {
@@ -121,56 +140,164 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
             if (active) {
                 const TileInfo rt = ti[sl.t_begin + t];
                 const PairRef r = ref_doubled(make_ref(rt.c0x, rt.c0y, rt.c0z, sx, sy, sz, a));
-                const int ybase = r.n0 - w;                    // band index of sample n0 + m is ybase + m
-                // one window: positions to walk Q (0: skip), its first sample's band row y0, the
-                // positions [qa, qa + span) this pass keeps (its band, inside the record; none when
-                // the window lies wholly in another pass's band), d_0, A / 2R and the exponent scale
-                struct Win { int Q, y0, qa, span; float d, wR, c2; };
+                const int ybase = r.n0 - w;                    // band row of sample n0 + m is ybase + m
+                // one window: sample pairs to walk NP (0: skip), the band row y0 of its first sample,
+                // its sample count, the scaled phase s and its step at that sample, the scaled weight
+                struct Win { int NP, y0, cnt; float s, step, wt; };
                 auto window = [&](int l) {
                     const FfGauss G = S.tile[b][l];
-                    Win w;
-                    w.Q = (int)G.e.w;
+                    Win c;
+                    c.NP = (int)G.e.w;
                     float invR, phi;
                     pair_phase_pre(r, G.o.x, G.o.y, G.o.z, G.o.w, invR, phi);
                     const float tt = phi * invDelta;
                     const float ulo = __fadd_ru(tt - G.e.z, FF_MAGIC);      // MAGIC + first window sample
                     const float uhi = __fadd_rd(tt + G.e.z, FF_MAGIC);      // MAGIC + last window sample
                     const int m0 = __float_as_int(ulo) - FF_MAGIC_BITS;
-                    const int cnt = __float_as_int(uhi) - __float_as_int(ulo) + 1;
-                    w.d = fmaf(-(ulo - FF_MAGIC), Delta, phi);
-                    w.y0 = ybase + m0;
-                    w.qa = max(0, -w.y0);
-                    w.span = max(0, min(cnt, LBe - w.y0) - w.qa);
-                    w.wR = G.e.x * invR;
-                    w.c2 = G.e.y;
-                    return w;
+                    c.cnt = max(0, __float_as_int(uhi) - __float_as_int(ulo) + 1);
+                    c.y0 = ybase + m0;
+                    c.s = G.e.y * fmaf(-(ulo - FF_MAGIC), Delta, phi);
+                    c.step = G.e.y * Delta;
+                    c.wt = G.e.x * invR;
+                    return c;
                 };
-                // the next Gaussian's window is formed while this one is walked
-                Win cur = window(0);
-#pragma unroll 1
-                for (int l = 0; l < TILE; ++l) {
-                    const Win nxt = window(l + 1 < TILE ? l + 1 : l);
-                    if (cur.Q > 0) {
-                        float d = cur.d;
-#pragma unroll 4
-                        for (int q = 0; q < cur.Q; ++q) {
-                            const float v = cur.wR * d * ex2_approx(d * d * cur.c2);
-                            if ((unsigned)(q - cur.qa) < (unsigned)cur.span) Y[(cur.y0 + q) * 32 + lane] += v;
-                            d -= Delta;
+                // two samples per step: rows 2i + 2p, 2i + 2p + 1 from the even row 2i at or below y0
+                auto walk_pairs = [&](const Win& c) {
+                    const int off = c.y0 & 1;
+                    float2* Yp = Y2 + ((c.y0 - off) >> 1) * 32;
+                    const float sa = fmaf((float)off, c.step, c.s);
+                    float2 s = make_float2(sa, sa - c.step);
+                    const float2 ds = make_float2(-2.f * c.step, -2.f * c.step);
+                    const float2 wt = make_float2(c.wt, c.wt);
+                    const unsigned cnt = (unsigned)c.cnt;
+                    auto pair = [&](int p, bool masked) {
+                        const float2 q = __fmul2_rn(s, s);
+                        float2 v = __fmul2_rn(s, wt);
+                        const float2 e = make_float2(ex2_approx(-q.x), ex2_approx(-q.y));
+                        if (masked) {      // window position of the pair's first sample: 2p - off
+                            const int m = 2 * p - off;
+                            v.x = (unsigned)m < cnt ? v.x : 0.f;
+                            v.y = (unsigned)(m + 1) < cnt ? v.y : 0.f;
                         }
+                        Yp[p * 32] = __ffma2_rn(v, e, Yp[p * 32]);
+                        s = __fadd2_rn(s, ds);
+                    };
+                    const int NP = c.NP;
+                    pair(0, true);
+#pragma unroll 4
+                    for (int p = 1; p < NP - 3; ++p) pair(p, false);
+                    for (int p = max(1, NP - 3); p < NP; ++p) pair(p, true);
+                };
+                // the same walk with every pair tested against the window and the band: a pair
+                // outside the band [0, LB) (pairs never straddle its ends: the walk starts at an
+                // even row and LB is even) adds zero to the lane's first pair of rows instead
+                auto walk_pairs_banded = [&](const Win& c) {
+                    const int off = c.y0 & 1, ya = c.y0 - off;
+                    const float sa = fmaf((float)off, c.step, c.s);
+                    float2 s = make_float2(sa, sa - c.step);
+                    const float2 ds = make_float2(-2.f * c.step, -2.f * c.step);
+                    const float2 wt = make_float2(c.wt, c.wt);
+                    const unsigned cnt = (unsigned)c.cnt;
+#pragma unroll 2
+                    for (int p = 0; p < c.NP; ++p) {
+                        const float2 q = __fmul2_rn(s, s);
+                        float2 v = __fmul2_rn(s, wt);
+                        const float2 e = make_float2(ex2_approx(-q.x), ex2_approx(-q.y));
+                        const int row = ya + 2 * p, m = 2 * p - off;
+                        const bool inb = (unsigned)row < (unsigned)LB;
+                        v.x = inb && (unsigned)m < cnt ? v.x : 0.f;
+                        v.y = inb && (unsigned)(m + 1) < cnt ? v.y : 0.f;
+                        float2* yp = Y2 + (inb ? (row >> 1) : 0) * 32;
+                        *yp = __ffma2_rn(v, e, *yp);
+                        s = __fadd2_rn(s, ds);
                     }
-                    cur = nxt;
+                };
+                // per Gaussian, one path for the whole warp: the plain paired walk when every lane's
+                // walked rows lie in its band, none when every lane's window lies wholly in another
+                // pass's samples, else the banded walk (a window across a pass boundary)
+                auto walk = [&](const Win& c) {
+                    if (c.NP > 0) {
+                        const int ya = c.y0 - (c.y0 & 1);      // first walked row
+                        const bool in = ya >= 0 && ya + 2 * c.NP <= LB;
+                        const bool out = ya >= LB || ya + 2 * c.NP <= 0;
+                        const unsigned am = __activemask();
+                        if (__all_sync(am, in)) walk_pairs(c);
+                        else if (!__all_sync(am, out)) walk_pairs_banded(c);
+                    }
+                };
+                // the windows of the next FF_G Gaussians are formed while the current FF_G are walked:
+                // independent chains of phase, bounds and weight that hide one another's latency
+                Win cur[FF_G];
+#pragma unroll
+                for (int u = 0; u < FF_G; ++u) cur[u] = window(u);
+#pragma unroll 1
+                for (int l = 0; l < TILE; l += FF_G) {
+                    Win nxt[FF_G];
+#pragma unroll
+                    for (int u = 0; u < FF_G; ++u) nxt[u] = window(min(l + FF_G + u, TILE - 1));
+#pragma unroll
+                    for (int u = 0; u < FF_G; ++u) walk(cur[u]);
+#pragma unroll
+                    for (int u = 0; u < FF_G; ++u) cur[u] = nxt[u];
                 }
             }
             __syncthreads();      // tile t's buffer is free; tile t + 1 is staged
         }
         if (active) {      // row positions [pass LB, pass LB + LB): LB and PL are multiples of 4
             float4* dst = reinterpret_cast<float4*>(prow + pass * LB);
-            for (int q = 0; q < LBe; q += 4)
-                dst[q >> 2] = make_float4(Y[q * 32 + lane], Y[(q + 1) * 32 + lane], Y[(q + 2) * 32 + lane],
-                                          Y[(q + 3) * 32 + lane]);
+            for (int q = 0; q < LBe; q += 4) {
+                const float2 u0 = Y2[(q >> 1) * 32], u1 = Y2[((q >> 1) + 1) * 32];
+                dst[q >> 2] = make_float4(u0.x, u0.y, u1.x, u1.y);
+            }
         }
         __syncthreads();
+    }
+}
+
+// Longest slabs first: the slab descriptors permuted in place by decreasing box diagonal (ties
+// by index), so that the CTAs of the slabs with the longest sample bands -- those that may need
+// several passes, such as a tile range that jumps across the Morton order -- start in the first
+// wave instead of extending the last.  The slab reduction sums the rows of all slabs, so only the
+// order of its (fixed-order) sum changes.  One CTA; S <= FF_ORDER_MAX.
+constexpr int FF_ORDER_THREADS = 1024;
+constexpr int FF_ORDER_MAX = 2048;
+constexpr int FF_ORDER_PER = FF_ORDER_MAX / FF_ORDER_THREADS;
+
+__global__ void __launch_bounds__(FF_ORDER_THREADS)
+slab_order_kernel(SlabInfo* __restrict__ si, int S) {
+    __shared__ float key[FF_ORDER_MAX];
+    SlabInfo mine[FF_ORDER_PER];
+    int rank[FF_ORDER_PER];
+#pragma unroll
+    for (int u = 0; u < FF_ORDER_PER; ++u) {
+        const int s = threadIdx.x + u * FF_ORDER_THREADS;
+        if (s < S) {
+            mine[u] = si[s];
+            const float dx = mine[u].hi[0] - mine[u].lo[0], dy = mine[u].hi[1] - mine[u].lo[1],
+                        dz = mine[u].hi[2] - mine[u].lo[2];
+            key[s] = (mine[u].t_end > mine[u].t_begin) ? dx * dx + dy * dy + dz * dz : -1.f;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < FF_ORDER_PER; ++u) {
+        const int s = threadIdx.x + u * FF_ORDER_THREADS;
+        rank[u] = 0;
+        if (s < S) {
+            const float k = key[s];
+            int r = 0;
+            for (int t = 0; t < S; ++t) {
+                const float kt = key[t];
+                r += (kt > k) || (kt == k && t < s);
+            }
+            rank[u] = r;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < FF_ORDER_PER; ++u) {
+        const int s = threadIdx.x + u * FF_ORDER_THREADS;
+        if (s < S) si[rank[u]] = mine[u];
     }
 }
 
@@ -178,6 +305,12 @@ fwd_free_lanes_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, con
 // Host side.
 
 size_t fwd_free_smem(int NW, int LB) { return ff_smem_bytes(NW, LB); }
+
+cudaError_t launch_slab_order(SlabInfo* si, int S, cudaStream_t st) {
+    if (S <= 1 || S > FF_ORDER_MAX) return cudaSuccess;     // more slabs: kept in tile order
+    slab_order_kernel<<<1, FF_ORDER_THREADS, 0, st>>>(si, S);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_forward_free(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
                                 float* partial, int2* rows, int PL, int LB, int NW, cudaStream_t st) {

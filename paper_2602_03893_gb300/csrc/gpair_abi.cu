@@ -24,6 +24,7 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st);
 size_t fwd_free_smem(int NW, int LB);
+cudaError_t launch_slab_order(SlabInfo* si, int S, cudaStream_t st);
 size_t spatial_order_bytes(int64_t M);
 cudaError_t launch_spatial_order(const GaussDev& g, void* scratch, GaussDev& gp, cudaStream_t st);
 cudaError_t launch_forward_free(const GaussDev& g, const ArrDev& a, const TileInfo* ti, const SlabInfo* si, int S,
@@ -481,6 +482,7 @@ gpair_status run_forward(const GaussDev& g, const ArrDev& a, float* y, cudaStrea
         e = launch_spatial_order(g, base + p.off_sort, gp, st);
         if (e == cudaSuccess) e = launch_tile_info(gp, ti, st);
         if (e == cudaSuccess) e = launch_slab_info_soa(gp, gp.ntiles, p.tiles_per_slab, p.S, si, st);
+        if (e == cudaSuccess) e = launch_slab_order(si, p.S, st);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], st);
         if (e == cudaSuccess) e = launch_forward_free(gp, a, ti, si, p.S, part, rows, p.PL, p.LB, p.NW, st);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
