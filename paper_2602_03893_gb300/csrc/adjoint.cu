@@ -254,7 +254,12 @@ adj_kernel(GaussDev g, ArrDev a, const TileInfo* __restrict__ ti, const float* _
 //     Q_p[b] = sum_{m < L} delta[b + m] c[m][p],
 // so one table of L-tap correlations per sensor replaces the per-sample evaluation.
 
-// Q[j][b + L][p] for window starts b in [-L, N_t): the residual is zero outside the record.
+// The table is split by term so that a warp's gathers of nearby window starts touch as few
+// cache lines as possible: Qa[j][b + L] holds Q_0 .. Q_3 (16 bytes), Qb[j][b + L] the rest (Q_4,
+// Q_5 as 8 bytes for P = 6; Q_4 .. Q_7 as 16 bytes for P = 7, 8), for window starts b in
+// [-L, N_t); the residual is zero outside the record.  Qb starts N_d (N_t + L) float4 after Qa.
+__host__ __device__ __forceinline__ size_t adj_qb_offset(int Nd, int Nt, int L) { return (size_t)Nd * (Nt + L); }
+
 template <int P>
 __global__ void __launch_bounds__(256)
 adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ MomentTable T, float* __restrict__ Q) {
@@ -278,14 +283,16 @@ adj_q_kernel(const float* __restrict__ delta, int Nt, const __grid_constant__ Mo
 #pragma unroll
         for (int p = 0; p < P; ++p) acc[p] = fmaf(dl, T.c[m][p], acc[p]);
     }
-    float4* dst = reinterpret_cast<float4*>(Q + ((size_t)j * (Nt + L) + (b + L)) * MOM_P);
-    dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    const size_t e = (size_t)j * (Nt + L) + (b + L);
+    float4* Qa = reinterpret_cast<float4*>(Q);
+    Qa[e] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    if constexpr (P == 6) reinterpret_cast<float2*>(Qa + adj_qb_offset(gridDim.y, Nt, L))[e] = make_float2(acc[4], acc[5]);
+    else (Qa + adj_qb_offset(gridDim.y, Nt, L))[e] = make_float4(acc[4], acc[5], acc[6], acc[7]);
 }
 
 // One CTA per brick of 256 grid Gaussians, one thread per Gaussian, all sensors in chunks of 32.
 template <int P>
-__global__ void __launch_bounds__(ADJ_THREADS)
+__global__ void __launch_bounds__(ADJ_THREADS, 5)
 adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const float* __restrict__ Q,
                   const __grid_constant__ MomentTable T, float* __restrict__ gA) {
     __shared__ PairRef refs2[2][ADJ_SC];
@@ -306,6 +313,8 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
     const float ED = (float)T.E * Delta;
     const float ksi = ks * invDelta;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // references below carry 2 (c0 - s)
+    const float4* Qa = reinterpret_cast<const float4*>(Q);
+    const size_t qb_off = adj_qb_offset(a.Nd, Nt, L);
     KahanF kA;
     // References are double-buffered: after each barrier the last warp forms the next chunk's
     // FP64 references while the others already work on the current chunk.
@@ -333,13 +342,17 @@ adj_moment_kernel(GaussDev g, ArrDev a, const float* __restrict__ delta, const f
                 if (b < -L || b >= Nt) continue;
                 const float d0 = fmaf(-mf, Delta, phi);
                 const float e = (d0 - T.dstar) * T.inv_half;
-                const float4* qp = reinterpret_cast<const float4*>(Q + ((size_t)(j0 + q) * (Nt + L) + (b + L)) * MOM_P);
-                const float4 q0 = __ldg(qp), q1 = __ldg(qp + 1);
+                const size_t qe = (size_t)(j0 + q) * (Nt + L) + (b + L);
+                const float4 q0 = __ldg(Qa + qe);
                 float s;
-                if constexpr (P == 8) s = fmaf(fmaf(q1.w, e, q1.z), e, q1.y);
-                else if constexpr (P == 7) s = fmaf(q1.z, e, q1.y);
-                else s = q1.y;
-                s = fmaf(s, e, q1.x);
+                if constexpr (P == 6) {
+                    const float2 q1 = __ldg(reinterpret_cast<const float2*>(Qa + qb_off) + qe);
+                    s = fmaf(q1.y, e, q1.x);
+                } else {
+                    const float4 q1 = __ldg(Qa + qb_off + qe);
+                    if constexpr (P == 8) s = fmaf(fmaf(fmaf(q1.w, e, q1.z), e, q1.y), e, q1.x);
+                    else s = fmaf(fmaf(q1.z, e, q1.y), e, q1.x);
+                }
                 s = fmaf(s, e, q0.w);
                 s = fmaf(s, e, q0.z);
                 s = fmaf(s, e, q0.y);
