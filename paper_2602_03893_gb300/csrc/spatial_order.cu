@@ -112,28 +112,42 @@ __global__ void so_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int
     for (int d = threadIdx.x; d < SO_RADIX; d += SO_THREADS) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// Step 2: exclusive scan of the counts in (digit, block) order, one block with a thread per
-// digit: thread d scans its own row of per-block counts, then the block scans the digit totals.
-__global__ void so_scan_kernel(int* __restrict__ hist, int nb) {
-    __shared__ int tot[SO_RADIX];
-    const int d = threadIdx.x;
-    int* row = hist + (size_t)d * nb;
+// Step 2: exclusive scan of the counts in (digit, block) order, i.e. of hist as one flat array.
+// One block: each thread sums a contiguous segment (independent loads), the block scans the
+// segment sums with warp shuffles, and each thread writes its segment's running offsets.
+constexpr int SO_SCAN_THREADS = 1024;
+__global__ void __launch_bounds__(SO_SCAN_THREADS) so_scan_kernel(int* __restrict__ hist, int nb) {
+    __shared__ int wsum[SO_SCAN_THREADS / 32];
+    const int64_t N = (int64_t)SO_RADIX * nb;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t per = (N + SO_SCAN_THREADS - 1) / SO_SCAN_THREADS;
+    const int64_t a = t * per, b = a + per < N ? a + per : N;
     int s = 0;
-    for (int b = 0; b < nb; ++b) {
-        const int c = row[b];
-        row[b] = s;
-        s += c;
+    for (int64_t i = a; i < b; ++i) s += hist[i];
+    int v = s;                                  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
-    tot[d] = s;
+    if (lane == 31) wsum[w] = v;
     __syncthreads();
-    for (int off = 1; off < SO_RADIX; off <<= 1) {    // inclusive scan of the digit totals
-        const int v = d >= off ? tot[d - off] : 0;
-        __syncthreads();
-        tot[d] += v;
-        __syncthreads();
+    if (w == 0) {                               // inclusive scan of the warp totals
+        int x = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        wsum[lane] = x;
     }
-    const int before = d ? tot[d - 1] : 0;
-    for (int b = 0; b < nb; ++b) row[b] += before;
+    __syncthreads();
+    int run = v - s + (w ? wsum[w - 1] : 0);    // exclusive offset of this thread's segment
+    for (int64_t i = a; i < b; ++i) {
+        const int c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
 }
 
 // Step 3: stable scatter.  The block takes its keys 256 at a time in index order; inside a warp
@@ -219,7 +233,7 @@ cudaError_t launch_spatial_order(const GaussDev& g, void* scratch, GaussDev& gp,
     for (int pass = 0; pass < SO_PASSES; ++pass) {
         const int in = pass & 1;
         so_hist_kernel<<<nb, SO_THREADS, 0, st>>>(keys[in], M, SO_DIGIT * pass, hist);
-        so_scan_kernel<<<1, SO_RADIX, 0, st>>>(hist, nb);
+        so_scan_kernel<<<1, SO_SCAN_THREADS, 0, st>>>(hist, nb);
         so_scatter_kernel<<<nb, SO_THREADS, 0, st>>>(keys[in], vals[in], M, SO_DIGIT * pass, hist, keys[in ^ 1],
                                                      vals[in ^ 1]);
     }
