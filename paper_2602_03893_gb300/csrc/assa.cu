@@ -305,11 +305,16 @@ assa_adj_kernel(GaussDev g, ArrDev a, const float* __restrict__ dconv, const __g
     const int64_t t = blockIdx.x;
     const int l = threadIdx.x, warp = l >> 5, lane = l & 31;
     const int tx = (int)(t % g.ntx), ty = (int)((t / g.ntx) % g.nty), tz = (int)(t / ((int64_t)g.ntx * g.nty));
-    const int gx = tx * BX + (l & (BX - 1)), gy = ty * BY + ((l / BX) & (BY - 1)), gz = tz * BZ + l / (BX * BY);
+    // warp w takes a 4 x 4 x 2 block of the 8 x 8 x 4 brick, so that the snapped positions of its
+    // 32 Gaussians for one sensor -- the residual entries it gathers -- stay close together
+    static_assert(BX == 8 && BY == 8 && BZ == 4 && TILE == 256, "brick of 8 x 8 x 4, 8 warps");
+    const int lx = (l & 3) | (((l >> 5) & 1) << 2), ly = ((l >> 2) & 3) | (((l >> 6) & 1) << 2),
+              lz = ((l >> 4) & 1) | (((l >> 7) & 1) << 1);
+    const int gx = tx * BX + lx, gy = ty * BY + ly, gz = tz * BZ + lz;
     const bool valid = gx < g.nx && gy < g.ny && gz < g.nz;
     const int64_t i = ((int64_t)gz * g.ny + gy) * g.nx + gx;
-    float dx, dy, dz;
-    brick_offset(l, g.h, dx, dy, dz);
+    const float dx = ((float)lx - 0.5f * (BX - 1)) * g.h, dy = ((float)ly - 0.5f * (BY - 1)) * g.h,
+                dz = ((float)lz - 0.5f * (BZ - 1)) * g.h;
     const double c0x = g.ox + (tx * BX + BX / 2) * (double)g.h;
     const double c0y = g.oy + (ty * BY + BY / 2) * (double)g.h;
     const double c0z = g.oz + (tz * BZ + BZ / 2) * (double)g.h;
