@@ -567,7 +567,7 @@ def main():
         xbytes = 8.0 * w.M      # amplitudes in, volume out
         vox = {"ms": xms, "alg_bytes": xbytes, "achieved_GBs": xbytes / (xms / 1e3) / 1e9, "peak_GBs": HBM_GBS,
                "frac": xbytes / (xms / 1e3) / 1e9 / HBM_GBS,
-               "includes": "gpair_voxelize, lattice case: three separable passes (24 B per voxel moved)"}
+               "includes": "gpair_voxelize, lattice case: the three separable passes fused in one kernel (the volume read and written once)"}
         dims = (g.nz, g.ny, g.nx)
         rng_max = float(A_true.max())
         vals, times = None, []

@@ -97,9 +97,94 @@ vox_pass_run_kernel(const float* __restrict__ in, float* __restrict__ out, int n
     }
 }
 
+// All three passes in one kernel, for taps fixed at compile time.  A CTA owns a column block of
+// VF_TX x VF_TY outputs and VF_TZ planes, one thread per (x, y) column, and marches z through the
+// VF_TZ + 2 MM input planes it needs: each plane's input patch (with an MM halo in x and y, zero
+// outside the volume) is staged in shared memory, convolved along x into a second buffer, then
+// along y by each thread for its own column; the last 2 MM + 1 such values stay in registers,
+// and once a plane's z neighbours are in, the thread writes its output.  The volume is read once
+// from DRAM and written once (the halos come from L2), instead of three reads and writes through
+// a scratch volume.  Each output is the same three sums as the separate passes', in the same
+// order, so the result is the same.
+constexpr int VF_TX = 32, VF_TY = 8, VF_TZ = 16;
+constexpr int VF_THREADS = VF_TX * VF_TY;
+
+template <int MM>
+__global__ void __launch_bounds__(VF_THREADS, 4)
+vox_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz, Taps taps) {
+    constexpr int PX = VF_TX + 2 * MM, PY = VF_TY + 2 * MM, NPATCH = PX * PY;
+    constexpr int NLOAD = (NPATCH + VF_THREADS - 1) / VF_THREADS;            // patch values per thread
+    constexpr int NXP = (PY * VF_TX + VF_THREADS - 1) / VF_THREADS;          // x-pass outputs per thread
+    constexpr int NR = 2 * MM + 1;                                          // taps, and planes in the ring
+    __shared__ float P[PY][PX];
+    __shared__ float Sx[PY][VF_TX];
+    const int t = threadIdx.x, tx = t % VF_TX, ty = t / VF_TX;
+    const int x0 = blockIdx.x * VF_TX, y0 = blockIdx.y * VF_TY, z0 = blockIdx.z * VF_TZ;
+    const int64_t plane = (int64_t)nx * ny;
+    // this thread's patch values of input plane zi (zero outside the volume)
+    auto load = [&](int zi, float (&v)[NLOAD]) {
+#pragma unroll
+        for (int u = 0; u < NLOAD; ++u) {
+            const int q = t + u * VF_THREADS;
+            const int px = q % PX, py = q / PX;
+            const int gx = x0 - MM + px, gy = y0 - MM + py;
+            const bool ok = q < NPATCH && (unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny &&
+                            (unsigned)zi < (unsigned)nz;
+            v[u] = ok ? __ldg(in + zi * plane + (int64_t)gy * nx + gx) : 0.f;
+        }
+    };
+    float pre[NLOAD];
+    load(z0 - MM, pre);
+    float ring[NR];                          // ring[NR - 1] is the newest plane's value
+#pragma unroll
+    for (int m = 0; m < NR; ++m) ring[m] = 0.f;
+    const bool own = x0 + tx < nx && y0 + ty < ny;
+#pragma unroll 1
+    for (int i = 0; i < VF_TZ + 2 * MM; ++i) {
+        __syncthreads();      // the previous plane's x pass is done with P, its y pass with Sx
+#pragma unroll
+        for (int u = 0; u < NLOAD; ++u) {
+            const int q = t + u * VF_THREADS;
+            if (q < NPATCH) P[q / PX][q % PX] = pre[u];
+        }
+        __syncthreads();
+        if (i + 1 < VF_TZ + 2 * MM) load(z0 - MM + i + 1, pre);      // the next plane, in flight meanwhile
+#pragma unroll
+        for (int u = 0; u < NXP; ++u) {
+            const int q = t + u * VF_THREADS;
+            if (q < PY * VF_TX) {
+                const int r = q / VF_TX, x = q % VF_TX;
+                float acc = 0.f;
+#pragma unroll
+                for (int m = 0; m < NR; ++m) acc = fmaf(taps.t[m], P[r][x + m], acc);
+                Sx[r][x] = acc;
+            }
+        }
+        __syncthreads();
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 0; m < NR; ++m) acc = fmaf(taps.t[m], Sx[ty + m][tx], acc);
+#pragma unroll
+        for (int m = 0; m < NR - 1; ++m) ring[m] = ring[m + 1];
+        ring[NR - 1] = acc;                  // the (x, y)-convolved value of plane z0 - MM + i
+        if (i >= 2 * MM) {                   // plane zo = z0 + i - 2 MM has all its z neighbours
+            const int zo = z0 + i - 2 * MM;
+            float o = 0.f;
+#pragma unroll
+            for (int m = 0; m < NR; ++m) o = fmaf(taps.t[m], ring[m], o);
+            if (own && zo < nz) out[zo * plane + (int64_t)(y0 + ty) * nx + x0 + tx] = o;
+        }
+    }
+}
+
 template <int MM>
 static void vox_passes_fixed(const float* A, float* vol, float* tmp, const gpair_grid& og, const Taps& taps,
                              dim3 grid, cudaStream_t st) {
+    const dim3 fgrid((og.nx + VF_TX - 1) / VF_TX, (og.ny + VF_TY - 1) / VF_TY, (og.nz + VF_TZ - 1) / VF_TZ);
+    if (fgrid.y <= 65535 && fgrid.z <= 65535) {
+        vox_fused_kernel<MM><<<fgrid, VF_THREADS, 0, st>>>(A, vol, og.nx, og.ny, og.nz, taps);
+        return;
+    }
     vox_pass_fixed_kernel<0, MM><<<grid, VOX_THREADS, 0, st>>>(A, vol, og.nx, og.ny, og.nz, taps);
     const int64_t gy = (int64_t)((og.ny + VOX_RUN - 1) / VOX_RUN) * og.nz;
     const int64_t gz = (int64_t)((og.nz + VOX_RUN - 1) / VOX_RUN) * og.ny;
