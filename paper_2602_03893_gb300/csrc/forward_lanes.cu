@@ -400,35 +400,34 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         if (active && cube_on) {
         if constexpr (LF > 0) {
         // correlation of the cube's moment band into the signal band, bin by bin: bin b adds
-        // c[m] . Z[b] to output b + m for m < LF; acc[s] holds the output n with n = s (mod LF),
-        // and output b is complete once bin b is in.  Each bin is cleared as it is read.
+        // c[m] . Z[b] to output b + m for m < LF; acc[m] holds output b + m, so output b (acc[0])
+        // is complete once bin b is in, and the ring shifts by one (the bin loop unrolled by 4, so
+        // that most of the shift is register renaming).  Each bin is cleared as it is read.
         float acc[LF];
 #pragma unroll
         for (int q = 0; q < LF; ++q) acc[q] = 0.f;
-        for (int b0 = 0; b0 < NZ; b0 += LF) {
+#pragma unroll 4
+        for (int b = 0; b < NZ; ++b) {
+            float z[8];
+            Z.load(b * 32 + lane, z);
+            Z.clear(b * 32 + lane);
 #pragma unroll
-            for (int bb = 0; bb < LF; ++bb) {
-                const int b = b0 + bb;
-                if (b >= NZ) break;
-                float z[8];
-                Z.load(b * 32 + lane, z);
-                Z.clear(b * 32 + lane);
+            for (int m = 0; m < LF; ++m) {
+                float v = acc[m];
 #pragma unroll
-                for (int m = 0; m < LF; ++m) {
-                    float v = acc[(bb + m) & (LF - 1)];
-#pragma unroll
-                    for (int p = 0; p < P; ++p) v = fmaf(T.c[m][p], z[p], v);
-                    acc[(bb + m) & (LF - 1)] = v;
-                }
-                const int yi = yoff + b;
-                if ((unsigned)yi < (unsigned)LBe) Y[yi * 32 + lane] += acc[bb];
-                acc[bb] = 0.f;
+                for (int p = 0; p < P; ++p) v = fmaf(T.c[m][p], z[p], v);
+                acc[m] = v;
             }
-        }
-        // outputs NZ .. NZ + L - 2 are still in their slots
+            const int yi = yoff + b;
+            if ((unsigned)yi < (unsigned)LBe) Y[yi * 32 + lane] += acc[0];
 #pragma unroll
-        for (int q = 0; q < LF; ++q) {
-            const int n = NZ + ((q - NZ) & (LF - 1));
+            for (int m = 0; m < LF - 1; ++m) acc[m] = acc[m + 1];
+            acc[LF - 1] = 0.f;
+        }
+        // outputs NZ .. NZ + L - 2 are in acc[0 .. L - 2]
+#pragma unroll
+        for (int q = 0; q < LF - 1; ++q) {
+            const int n = NZ + q;
             const int yi = yoff + n;
             if (n < NO && (unsigned)yi < (unsigned)LBe) Y[yi * 32 + lane] += acc[q];
         }
