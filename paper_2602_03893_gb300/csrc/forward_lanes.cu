@@ -401,12 +401,12 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
         if constexpr (LF > 0) {
         // correlation of the cube's moment band into the signal band, bin by bin: bin b adds
         // c[m] . Z[b] to output b + m for m < LF; acc[m] holds output b + m, so output b (acc[0])
-        // is complete once bin b is in, and the ring shifts by one (the bin loop unrolled by 4, so
-        // that most of the shift is register renaming).  Each bin is cleared as it is read.
+        // is complete once bin b is in, and the ring shifts by one (the bin loop unrolled by 2, so
+        // that half of the shift is register renaming).  Each bin is cleared as it is read.
         float acc[LF];
 #pragma unroll
         for (int q = 0; q < LF; ++q) acc[q] = 0.f;
-#pragma unroll 4
+#pragma unroll 2
         for (int b = 0; b < NZ; ++b) {
             float z[8];
             Z.load(b * 32 + lane, z);
