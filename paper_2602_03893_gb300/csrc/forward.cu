@@ -1052,6 +1052,93 @@ slab_reduce_banded_kernel(const float* __restrict__ partial, const int2* __restr
     if (n < Nt) y[(size_t)j * Nt + n] = acc;
 }
 
+// Banded rows, one block per (sensor, group of four 256-sample chunks): the sensor's row
+// descriptors are sorted by band start (bitonic sort of (start, slab) keys in shared memory), and
+// each chunk walks only the slabs whose bands can reach it -- those starting after the chunk's
+// first sample minus the longest band and before its end, a contiguous run of the sorted keys --
+// instead of testing every slab, eight slabs' loads at a time.  Each sample sums its slabs in the
+// order of their band starts, ties by slab index: a fixed order, so the result is deterministic.
+constexpr int SRS_THREADS = 256;
+constexpr int SRS_MAX_S = 2048;             // sorted keys and descriptors: 32 KB
+constexpr int SRS_CHUNKS = 4;               // 256-sample chunks per block (blockIdx.y: chunk group)
+constexpr int SRS_UNROLL = 8;
+__global__ void __launch_bounds__(SRS_THREADS)
+slab_reduce_sorted_kernel(const float* __restrict__ partial, const int2* __restrict__ rows, int S, int Nd, int Nt,
+                          int PL, float* __restrict__ y) {
+    extern __shared__ unsigned long long srs_key[];     // [Sp] keys, then S descriptors
+    __shared__ int red[2][SRS_THREADS / 32];
+    const int j = blockIdx.x, t = threadIdx.x;
+    int Sp = 1;
+    while (Sp < S) Sp <<= 1;
+    int2* srow = reinterpret_cast<int2*>(srs_key + Sp);
+    int lbmax = 0, nvalid = 0;
+    for (int q = t; q < Sp; q += SRS_THREADS) {
+        unsigned long long k = ~0ull;                     // empty rows sort last
+        if (q < S) {
+            const int2 ri = rows[(size_t)q * Nd + j];
+            srow[q] = ri;
+            if (ri.y > 0) {
+                k = ((unsigned long long)(unsigned)ri.x << 32) | (unsigned)q;
+                lbmax = max(lbmax, ri.y);
+                ++nvalid;
+            }
+        }
+        srs_key[q] = k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lbmax = max(lbmax, __shfl_xor_sync(0xffffffffu, lbmax, o));
+        nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
+    }
+    if ((t & 31) == 0) { red[0][t >> 5] = lbmax; red[1][t >> 5] = nvalid; }
+    __syncthreads();
+    lbmax = 0; nvalid = 0;
+#pragma unroll
+    for (int w = 0; w < SRS_THREADS / 32; ++w) { lbmax = max(lbmax, red[0][w]); nvalid += red[1][w]; }
+    for (int k = 2; k <= Sp; k <<= 1)                     // bitonic sort, ascending
+        for (int h = k >> 1; h > 0; h >>= 1) {
+            for (int i = t; i < Sp; i += SRS_THREADS) {
+                const int p = i ^ h;
+                if (p > i) {
+                    const unsigned long long a = srs_key[i], b = srs_key[p];
+                    if ((a > b) == ((i & k) == 0)) { srs_key[i] = b; srs_key[p] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    const int c_end = min(Nt, (blockIdx.y + 1) * SRS_CHUNKS * SRS_THREADS);
+    for (int n0 = blockIdx.y * SRS_CHUNKS * SRS_THREADS; n0 < c_end; n0 += SRS_THREADS) {
+        // the run of keys whose bands can reach the chunk: start in [n0 - lbmax + 1, n0 + 256)
+        auto lower = [&](long long wv) {
+            int lo = 0, hi = nvalid;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)(srs_key[mid] >> 32) < wv) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+        };
+        const int i0 = lower((long long)n0 - lbmax + 1), i1 = lower((long long)n0 + SRS_THREADS);
+        const int n = n0 + t;
+        float acc = 0.f;
+        // SRS_UNROLL slabs at a time, so that their loads are in flight together; a slab past the
+        // run or missing the sample contributes an exact zero, so the sum is the slab-by-slab one
+        for (int i = i0; i < i1; i += SRS_UNROLL) {
+            float v[SRS_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SRS_UNROLL; ++u) {
+                const int ii = min(i + u, i1 - 1);
+                const unsigned long long k = srs_key[ii];
+                const int q = (int)(k & 0xffffffffu);
+                const unsigned d = (unsigned)(n - (int)(k >> 32));
+                const bool use = i + u < i1 && d < (unsigned)srow[q].y;
+                v[u] = use ? partial[((size_t)q * Nd + j) * PL + (use ? d : 0u)] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < SRS_UNROLL; ++u) acc += v[u];
+        }
+        if (n < Nt) y[(size_t)j * Nt + n] = acc;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Host side.
 
@@ -1138,11 +1225,24 @@ cudaError_t launch_forward(const GaussDev& g, const ArrDev& a, const TileInfo* t
     return cudaGetLastError();
 }
 
+static dim3 slab_reduce_sorted_grid(const ArrDev& a) {
+    return dim3(a.Nd, (a.Nt + SRS_CHUNKS * SRS_THREADS - 1) / (SRS_CHUNKS * SRS_THREADS));
+}
+
+static size_t slab_reduce_sorted_smem(int S) {
+    size_t Sp = 1;
+    while (Sp < (size_t)S) Sp <<= 1;
+    return Sp * sizeof(unsigned long long) + (size_t)S * sizeof(int2);
+}
+
 // Banded rows (start sample, length; row capacity PL) of any Gaussian set.
 cudaError_t launch_slab_reduce_rows(const ArrDev& a, const float* partial, const int2* rows, int S, int PL, float* y,
                                     cudaStream_t st) {
     dim3 rgrid((a.Nt + 255) / 256, a.Nd);
-    if (S <= SLAB_RED_MAX_S)
+    if (S <= SRS_MAX_S && slab_reduce_sorted_grid(a).y <= 65535)
+        slab_reduce_sorted_kernel<<<slab_reduce_sorted_grid(a), SRS_THREADS, slab_reduce_sorted_smem(S), st>>>(
+            partial, rows, S, a.Nd, a.Nt, PL, y);
+    else if (S <= SLAB_RED_MAX_S)
         slab_reduce_banded_kernel<<<rgrid, SLAB_RED_THREADS, (size_t)S * sizeof(int2), st>>>(partial, rows, S, a.Nd,
                                                                                              a.Nt, PL, y);
     else
@@ -1153,7 +1253,10 @@ cudaError_t launch_slab_reduce_rows(const ArrDev& a, const float* partial, const
 cudaError_t launch_slab_reduce(const GaussDev& g, const ArrDev& a, const float* partial, const int2* rows, int S,
                                int PL, float* y, cudaStream_t st) {
     dim3 rgrid((a.Nt + 255) / 256, a.Nd);
-    if (g.grid && S <= SLAB_RED_MAX_S)
+    if (g.grid && S <= SRS_MAX_S && slab_reduce_sorted_grid(a).y <= 65535)
+        slab_reduce_sorted_kernel<<<slab_reduce_sorted_grid(a), SRS_THREADS, slab_reduce_sorted_smem(S), st>>>(
+            partial, rows, S, a.Nd, a.Nt, PL, y);
+    else if (g.grid && S <= SLAB_RED_MAX_S)
         slab_reduce_banded_kernel<<<rgrid, SLAB_RED_THREADS, (size_t)S * sizeof(int2), st>>>(partial, rows, S, a.Nd,
                                                                                              a.Nt, PL, y);
     else
