@@ -42,6 +42,16 @@ def test_lattice_ragged_dims():
     assert rel_l2(_gpu_vox(w, g, 3.0), _ora_vox(w, g, 3.0)) < 1e-4
 
 
+@pytest.mark.parametrize("k", [1.5, 4.2, 5.5, 6.0, 7.5])
+def test_lattice_tap_counts_ragged(k):
+    """Tap counts 1, 4, 5 and 6 a side (the fused three-axis kernel) and 7 (the separate passes)
+    on a lattice whose sides are not multiples of the fused kernel's 32 x 8 x 16 block."""
+    g = synth.centred_grid(37, 19, 21, 0.1e-3)
+    A = np.random.default_rng(4).uniform(0, 1, g.M).astype(np.float32)
+    w = synth.Workload("ragged-taps", g, synth.cap_sensors(1, 5e-3, 10.0), 16, A=A)
+    assert rel_l2(_gpu_vox(w, g, k), _ora_vox(w, g, k)) < 1e-4
+
+
 def test_free_gaussians_scatter_path():
     g = synth.centred_grid(24, 20, 16, 0.1e-3)
     free = synth.free_gaussians(g, 3, A=np.random.default_rng(2).uniform(0, 1, g.M))
