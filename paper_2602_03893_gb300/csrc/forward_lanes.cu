@@ -232,7 +232,8 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
     const bool active = has_sensor && n_lo <= n_hi;
     if (active && n_hi + 1 - w > LB) set_status(status, DEV_CAPACITY);   // cannot happen with the host's LB
     const int LBe = active ? min(min(LB, a.Nt - w), n_hi + 1 - w) : 0;     // Y entries this lane keeps
-    if (has_sensor) rows[row] = make_int2(w, active ? min(LB, a.Nt - w) : 0);
+    // the row keeps the band's own samples only (the rest of the signal band stays zero)
+    if (has_sensor) rows[row] = make_int2(w, LBe);
 
     if (threadIdx.x == 0) {
         S.abort = 0;
@@ -493,7 +494,7 @@ fwd_lanes_kernel(GaussDev g, ArrDev a, const SlabInfo* __restrict__ slabs, float
     }
     if (active) {
         float4* prow = reinterpret_cast<float4*>(partial + row * LB);
-        for (int q = 0; q < LB; q += 4)
+        for (int q = 0; q < LBe; q += 4)      // LB is a multiple of 4, entries past LBe are zero
             prow[q >> 2] = make_float4(Y[q * 32 + lane], Y[(q + 1) * 32 + lane], Y[(q + 2) * 32 + lane],
                                        Y[(q + 3) * 32 + lane]);
     }
