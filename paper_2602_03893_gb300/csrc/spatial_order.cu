@@ -113,40 +113,55 @@ __global__ void so_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int
 }
 
 // Step 2: exclusive scan of the counts in (digit, block) order, i.e. of hist as one flat array.
-// One block: each thread sums a contiguous segment (independent loads), the block scans the
-// segment sums with warp shuffles, and each thread writes its segment's running offsets.
+// One block walks the array in tiles of SO_SCAN_THREADS x SO_SCAN_ITEMS entries: each thread loads
+// its SO_SCAN_ITEMS consecutive entries (all loads of a tile in flight together), the block scans
+// the thread sums with warp shuffles, and each thread writes its entries' running offsets; a
+// carry takes the tile's total to the next tile.
 constexpr int SO_SCAN_THREADS = 1024;
+constexpr int SO_SCAN_ITEMS = 8;
 __global__ void __launch_bounds__(SO_SCAN_THREADS) so_scan_kernel(int* __restrict__ hist, int nb) {
     __shared__ int wsum[SO_SCAN_THREADS / 32];
+    __shared__ int carry_s;
     const int64_t N = (int64_t)SO_RADIX * nb;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t per = (N + SO_SCAN_THREADS - 1) / SO_SCAN_THREADS;
-    const int64_t a = t * per, b = a + per < N ? a + per : N;
-    int s = 0;
-    for (int64_t i = a; i < b; ++i) s += hist[i];
-    int v = s;                                  // inclusive scan over the warp
+    constexpr int64_t TILE_N = (int64_t)SO_SCAN_THREADS * SO_SCAN_ITEMS;
+    int carry = 0;
+    for (int64_t base = 0; base < N; base += TILE_N) {
+        const int64_t a = base + (int64_t)t * SO_SCAN_ITEMS;
+        int v[SO_SCAN_ITEMS];
+        int s = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {                               // inclusive scan of the warp totals
-        int x = wsum[lane];
+        for (int k = 0; k < SO_SCAN_ITEMS; ++k) {
+            v[k] = a + k < N ? hist[a + k] : 0;
+            s += v[k];
+        }
+        int x = s;                                   // inclusive scan over the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += u;
         }
-        wsum[lane] = x;
-    }
-    __syncthreads();
-    int run = v - s + (w ? wsum[w - 1] : 0);    // exclusive offset of this thread's segment
-    for (int64_t i = a; i < b; ++i) {
-        const int c = hist[i];
-        hist[i] = run;
-        run += c;
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {                                // inclusive scan of the warp totals
+            int y = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += u;
+            }
+            wsum[lane] = y;
+            if (lane == 31) carry_s = y;             // the tile's total
+        }
+        __syncthreads();
+        int run = carry + x - s + (w ? wsum[w - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < SO_SCAN_ITEMS; ++k) {
+            if (a + k < N) hist[a + k] = run;
+            run += v[k];
+        }
+        carry += carry_s;
+        __syncthreads();                             // wsum and carry_s are reused by the next tile
     }
 }
 
