@@ -21,12 +21,13 @@
 // are masked.  When a lane's walked rows do not all lie in its band (a window across a pass
 // boundary or the record's start), the warp walks that Gaussian with every pair tested against
 // the band and the window; a window that lies wholly in another pass's samples is skipped.  Rows
-// past the band's kept entries are never written out.  The windows of the next FF_G Gaussians (phase,
-// bounds and weight: a chain of about twenty dependent operations with two MUFU operations
-// each) are formed together while the current FF_G are walked, so that their latencies overlap.
+// past the band's kept entries are never written out.  The windows of the next FF_G Gaussians
+// (phase, bounds and weight: a chain of about twenty dependent operations with two MUFU
+// operations each) are formed together while the current FF_G are walked, so that their
+// latencies overlap.
 //
 // After the slab each lane writes its band as the slab's banded partial row (start sample,
-// length); the slab reduction sums the rows per sample in fixed slab order.  No atomics.  A
+// length); the slab reduction sums the rows per sample in a fixed order.  No atomics.  A
 // sensor whose band is longer than the shared-memory band takes several passes over the slab,
 // each keeping the next LB samples.
 #include <cuda.h>

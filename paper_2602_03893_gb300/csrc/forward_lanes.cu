@@ -15,7 +15,7 @@
 //     y[n] += sum_{m < L} sum_p c[m][p] Z_p[n - m],
 // into its signal band for the slab ([sample][lane], also conflict free), then clears the
 // moment band.  After the slab the signal bands become the slab's partial rows, which the slab
-// reduction sums per sample in fixed slab order: no global atomics, deterministic.
+// reduction sums per sample in a fixed order: no global atomics, deterministic.
 #include <cuda.h>
 
 #include <climits>
