@@ -627,6 +627,16 @@ def main():
     roofline["fwd_plus_adj_frac_of_measured"] = ((kern["forward"]["t_bound_measured_s"] +
                                                   kern["adjoint"]["t_bound_measured_s"]) / (fwd_avg + adj_avg))
     roofline["pipe_peaks_measured"] = pipe_peaks
+    # the dominant kernel's algorithmic bytes per launch, beside the measured traffic: the forward
+    # reads the amplitudes and writes y (through its slab partial rows); the adjoint reads the
+    # residual and writes the amplitude gradient
+    alg_bytes = 4.0 * (w.M + w.Nd * w.Nt)
+    roofline["traffic_alg_bytes"] = alg_bytes
+    if tr:
+        roofline["traffic_over_alg"] = tr / alg_bytes
+        roofline["traffic_note"] = ("forward: the amplitudes read once, the rest the slab partial rows (each row "
+                                    "its own band of samples), summed into y by the slab reduction"
+                                    if dom == "forward" else "adjoint: the residual table is served from L2")
     if clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = kd["frac"] * SM_MAX_MHZ / clocks["sm_mhz"]
 
