@@ -219,14 +219,15 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, src):
-    """dram bytes per launch from the committed ncu summary, if it was taken on this source."""
+def profiled_traffic(kernel, src, workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken on this source and
+    this workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(kernel)
-        if e and e.get("src_hash") == src:
+        if e and e.get("src_hash") == src and e.get("workload") == workload:
             return e.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -612,7 +613,7 @@ def main():
                     "t_bound_measured_s": max(F / (pipe_peaks["fp32"] * 1e12), X / (pipe_peaks["mufu"] * 1e12))}
     dom = "forward" if fwd_avg >= adj_avg else "adjoint"
     src = src_hash("forward_lanes.cu" if dom == "forward" else "adjoint.cu", "gpair_internal.cuh")
-    tr = profiled_traffic(kern[dom]["kernel"], src)
+    tr = profiled_traffic(kern[dom]["kernel"], src, w.name)
     kd = kern[dom]
     roofline = {"bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": "T lane-ops/s (" + ("FP32" if kd["bound_pipe"] == "fp32" else "MUFU") + ")",
